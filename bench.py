@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark: Trotter site-steps/s of the second-order Trotter-Suzuki step.
+
+Workload (one "step" of this benchmark): the 8192 x 8192 FP32 roofline grid
+(32 seed-placed Gaussians in V, one seed-random packet), run through the
+whole hot path: table preparation from V (FP64 -> rounded FP32 tables),
+200 second-order Trotter steps on the fused temporally blocked kernel, and
+the FP64-compensated observables.  Inputs (8 B/site state + 8 B/site V) live
+in HBM when the timed region starts; the 1.6 GB working set is larger than
+L2, so no flush is needed between steps.
+
+``value`` = grid sites x Trotter steps x ranks / wall time of the timed steps
+(CUDA events, max over ranks).  ``e2e`` = the same through the C ABI with
+pinned host buffers (host->device of state and V, device->host of the result
+state and observables inside the timed region).
+
+``--impl reference`` times the FP64 CPU oracle on this host's cores on a
+bounded sample of the same workload.  Multi-GPU runs are independent
+replicas (no collective in the data path; the method needs none on one GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Trotter site-steps/s"
+UNIT = "site-steps/s"
+TROTTER_STEPS = 200
+BYTES_PER_SITE_LAUNCH = 24      # read re, im, gamma_V, s_V; write re, im (FP32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192, help="grid side")
+    ap.add_argument("--K", type=int, default=0, help="fused depth (0 = library default)")
+    ap.add_argument("--trotter-steps", type=int, default=TROTTER_STEPS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    def __init__(self, world, local, backend):
+        self.world = world
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(n: int, seed: int, budget_s: float = 12.0, max_steps: int = 10):
+    """Time the FP64 oracle on the n x n workload with all host cores: one
+    step to calibrate, then as many steps (<= 10, the paper's ten
+    iterations) as fit the budget.  Returns (site-steps/s, cores, sample)."""
+    import oracle
+    from paper_1208_2407_gb300 import workloads as wl
+    cores = os.cpu_count() or 1
+    c = wl.roofline_grid(n=n, seed=seed, steps=1)
+    re, im, V = c["re"], c["im"], c["V"]
+    t0 = time.perf_counter()
+    re, im = oracle.evolve(re, im, V, c["dt"], c["theta"], 1, nthreads=cores)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(max_steps, budget_s / max(t1, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.evolve(re, im, V, c["dt"], c["theta"], steps, nthreads=cores)
+    dt = time.perf_counter() - t0
+    rate = n * n * steps / dt
+    return rate, cores, "%dx%d FP64 oracle, %d Trotter steps (of the %d per step), %d threads" % (
+        n, n, steps, TROTTER_STEPS, cores)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1208_2407_gb300 import workloads as wl
+    cores = os.cpu_count() or 1
+    n = args.n
+    c = wl.roofline_grid(n=n, seed=args.seed, steps=1)
+    re, im, V = c["re"], c["im"], c["V"]
+    # bounded sample per step: the oracle's Trotter steps that fit ~10 s / K steps
+    t0 = time.perf_counter()
+    oracle.evolve(re, im, V, c["dt"], c["theta"], 1, nthreads=cores)
+    t1 = time.perf_counter() - t0
+    per = int(max(1, min(10, (60.0 / max(1, args.steps + args.warmup)) / max(t1, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.evolve(re, im, V, c["dt"], c["theta"], 1, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.norm(*oracle.evolve(re, im, V, c["dt"], c["theta"], per, nthreads=cores))
+    el = time.perf_counter() - t0
+    value = n * n * per * args.steps / el
+    sample = "%dx%d FP64 oracle, %d Trotter steps per step (bounded sample of %d), %d threads" % (
+        n, n, per, TROTTER_STEPS, cores)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "roofline grid %dx%d, 32-Gaussian V, packet, FP64 CPU oracle" % (n, n),
+                   "n": n, "trotter_steps_per_step": per, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_1208_2407_gb300 import trotter
+    from paper_1208_2407_gb300 import workloads as wl
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = Dist(world, local, "nccl")
+    trotter.load()
+    n, T = args.n, args.trotter_steps
+    K = args.K
+    c = wl.roofline_grid(n=n, seed=args.seed + rank, steps=T)
+
+    # inputs resident in HBM
+    re0 = torch.from_numpy(c["re"].astype(np.float32)).cuda()
+    im0 = torch.from_numpy(c["im"].astype(np.float32)).cuda()
+    Vd = torch.from_numpy(c["V"]).cuda()
+    g = trotter.Grid(n, n, "f32")
+    stream = torch.cuda.current_stream()
+    sp = trotter.current_stream_ptr()
+
+    ev_pairs = []
+
+    def one_step(record):
+        g.set_state(re0, im0, stream=sp)
+        g.set_potential(Vd, c["dt"], c["theta"], stream=sp)
+        if record:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.evolve(T, K, stream=sp)
+            b.record(stream)
+            ev_pairs.append((a, b))
+        else:
+            g.evolve(T, K, stream=sp)
+        return g.observe(stream=sp)
+
+    for _ in range(args.warmup):
+        obs = one_step(False)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    trotter.ts_launch_count(reset=True)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        obs = one_step(True)
+    end.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    launches = trotter.ts_launch_count()
+    el_ms = start.elapsed_time(end)
+    el_ms = dist.max(el_ms)
+    evolve_ms = sum(a.elapsed_time(b) for a, b in ev_pairs)
+    k_eff = K if K > 0 else 4
+    fused_launches_per_step = (T + k_eff - 1) // k_eff
+    avg_launch_ms = evolve_ms / (fused_launches_per_step * args.steps)
+
+    site_steps = float(n) * n * T
+    value = site_steps * args.steps * world / (el_ms / 1e3)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        h_re = torch.from_numpy(c["re"].astype(np.float32)).pin_memory()
+        h_im = torch.from_numpy(c["im"].astype(np.float32)).pin_memory()
+        h_V = torch.from_numpy(c["V"]).pin_memory()
+        o_re = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        o_im = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        hp = lambda t: trotter._VP(t.data_ptr())
+
+        def e2e_step():
+            trotter.ts_set_state(g.handle, hp(h_re), hp(h_im), trotter.TS_F32, trotter.TS_HOST, sp)
+            trotter.ts_set_potential(g.handle, hp(h_V), trotter.TS_HOST, c["dt"], c["theta"], sp)
+            trotter.ts_evolve(g.handle, T, K, sp)
+            trotter.ts_get_state(g.handle, hp(o_re), hp(o_im), trotter.TS_F32, trotter.TS_HOST, sp)
+            return trotter.ts_observe(g.handle, sp)
+
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = dist.max(time.perf_counter() - t0)
+        e2e = {"value": site_steps * args.steps * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * n * (4 + 4 + 8)),
+               "d2h_bytes_per_step": int(n * n * (4 + 4) + 7 * 8)}
+
+    # ---- roofline of the dominant kernel (the fused K-step kernel) ----
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved_gbs = BYTES_PER_SITE_LAUNCH * float(n) * n / (avg_launch_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "kernel": "fused_kernel<%d>" % k_eff,
+                "avg_launch_ms": avg_launch_ms,
+                "algorithmic_bytes_per_launch": BYTES_PER_SITE_LAUNCH * n * n}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = oracle_sample(n, args.seed)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "roofline grid %dx%d FP32, 32-Gaussian V, seed-random packet, "
+                                   "%d Trotter steps per step" % (n, n, T),
+                       "n": n, "trotter_steps_per_step": T, "K": k_eff,
+                       "l2": "inputs larger than L2 (%.1f GB working set)" % (n * n * 28 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "obs_last": {"norm": obs["norm"], "energy": obs["e_kin"] + obs["e_pot"]},
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    dist.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

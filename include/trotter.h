@@ -1,0 +1,160 @@
+/*
+ * trotter.h -- C ABI of libtrotter.so: the second-order Trotter-Suzuki time
+ * step of one particle on a 2-D lattice, as hand-written CUDA for sm_103a.
+ *
+ * The method (Wittek & Cucchietti, "A Second-Order Distributed
+ * Trotter-Suzuki Solver with a Hybrid Kernel", Sec. 2): the tight-binding
+ * Hamiltonian H = H0 + H1 + H2 per dimension (diagonal potential, even and
+ * odd 2x2 hopping blocks); exp(-i H dt) is approximated by the symmetric
+ * product U2(dt) = U1^T(dt) U1(dt) (Eq. secondorder).  One step applies the
+ * pair rotations  a' = cos(theta) a + i sin(theta) b,
+ *                 b' = i sin(theta) a + cos(theta) b
+ * (the block exponential M of Sec. 2 with hopping -J and theta = J dt / 2)
+ * over X-even, X-odd, Y-even, Y-odd neighbour pairs, then the diagonal phase
+ * exp(-i V dt), then the four sweeps in reverse order.  Open boundaries: a
+ * site without a partner is left unchanged.  hbar = 1, lattice spacing 1.
+ *
+ * Conventions shared by every call:
+ *  - Dense host or device arrays are row-major, nx*ny elements, site (x, y)
+ *    at index y*nx + x; x is the contiguous axis.
+ *  - On the device a grid keeps separate real and imaginary planes with a
+ *    row pitch of ts_grid_layout()'s `pitch` elements (a multiple of 32).
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls marked "async" only enqueue work; errors of enqueued
+ *    kernels surface at the next call marked "syncs".
+ *  - No call throws, exits or aborts.  Every call returns a ts_status; on an
+ *    error ts_last_error() returns a message (thread-local, valid until the
+ *    calling thread's next call).
+ *  - A grid handle is not thread-safe: use one handle from one thread at a
+ *    time.  Distinct handles are independent.
+ *  - Ownership: the caller owns every buffer it passes in (host arrays and a
+ *    caller-supplied device slab); the library never frees caller memory.
+ */
+#ifndef TROTTER_H
+#define TROTTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TS_OK = 0,
+    TS_ERR_ARG = -1,          /* invalid argument (null pointer, bad size, ...) */
+    TS_ERR_OOM = -2,          /* device allocation failed or budget exceeded     */
+    TS_ERR_CUDA = -3,         /* a CUDA runtime call failed                      */
+    TS_ERR_BUSY = -4,         /* request can never fit the configured budget     */
+    TS_ERR_TIMEOUT = -5,      /* a bounded device or host wait gave up           */
+    TS_ERR_STATE = -6,        /* call not valid in the handle's current state    */
+    TS_ERR_UNSUPPORTED = -7   /* combination not implemented (e.g. dtype/path)   */
+} ts_status;
+
+typedef enum { TS_F32 = 0, TS_F64 = 1 } ts_dtype;
+typedef enum { TS_HOST = 0, TS_DEVICE = 1 } ts_mem;
+
+typedef struct ts_grid ts_grid;
+
+/* Device layout of a grid: all planes live in one slab.
+ *   pitch        row pitch of every plane, in elements (multiple of 32)
+ *   plane_bytes  bytes per plane (multiple of 256)
+ *   slab_bytes   total bytes: 7 planes (re, im, ping-pong re, im, the two
+ *                potential-phase tables, V) plus reduction scratch. */
+typedef struct {
+    int64_t nx, ny, pitch;
+    size_t plane_bytes, slab_bytes;
+    ts_dtype dtype;
+} ts_layout;
+
+/* Compute the layout of an nx x ny grid of `dtype` without allocating.
+ * Errors: TS_ERR_ARG if nx or ny < 1, nx or ny > 2^20, or out == NULL. */
+ts_status ts_grid_layout(int64_t nx, int64_t ny, ts_dtype dtype, ts_layout *out);
+
+/* Create a grid handle.  `slab` is a device pointer of at least
+ * ts_grid_layout().slab_bytes bytes, 256-byte aligned, owned by the caller
+ * (e.g. a torch tensor); pass NULL to have the library cudaMalloc (and later
+ * free) its own slab.  The state starts at zero and the potential at V = 0
+ * with dt = theta = 0 (identity step) until ts_set_potential is called.
+ * Errors: TS_ERR_ARG (sizes, alignment, slab too small), TS_ERR_OOM,
+ * TS_ERR_CUDA.  Syncs the device (allocation and zero-fill). */
+ts_status ts_create_grid(int64_t nx, int64_t ny, ts_dtype dtype, void *slab,
+                         size_t slab_bytes, ts_grid **out);
+
+/* Destroy a handle; frees only what the library allocated.  NULL is OK. */
+ts_status ts_destroy_grid(ts_grid *g);
+
+/* Query: the layout and the device pointers of the CURRENT state planes
+ * (they swap between the two ping-pong pairs as the fused path runs). */
+ts_status ts_grid_info(const ts_grid *g, ts_layout *layout, void **re, void **im);
+
+/* Set the state psi from dense arrays of `src_dtype` in host or device
+ * memory (nx*ny elements each).  FP64 input to an FP32 grid is rounded once
+ * to nearest on the device.  Host input is staged through the grid's own
+ * ping-pong planes, so no extra device memory is used.  Async for device
+ * input; for host input the copy is issued on `stream` and the call returns
+ * when the host buffer may be reused. */
+ts_status ts_set_state(ts_grid *g, const void *re, const void *im,
+                       ts_dtype src_dtype, ts_mem where, void *stream);
+
+/* Read the state into dense arrays of `dst_dtype` (host or device).  Syncs
+ * `stream`; reports TS_ERR_TIMEOUT if a bounded wait inside an earlier fused
+ * launch gave up, TS_ERR_CUDA for a failed earlier launch. */
+ts_status ts_get_state(ts_grid *g, void *re, void *im, ts_dtype dst_dtype,
+                       ts_mem where, void *stream);
+
+/* Table preparation (Sec. 2: the external potential is one diagonal factor
+ * exp(-i V dt) per step).  V: dense FP64 array of nx*ny potential values in
+ * host or device memory, or NULL for V = 0.  dt: the time step; theta: the
+ * kinetic half-step angle J*dt/2 (hopping J = 2 theta / dt).  On the device
+ * the per-site table (gamma_V = 1 - cos(V dt), s_V = sin(V dt)) is computed
+ * in FP64 and rounded once to the grid's dtype; the kinetic rotation is
+ * applied in the same versine form (1 - cos theta, sin theta), computed in
+ * FP64 and rounded once.  Async (host V: returns when V may be reused). */
+ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
+                           double theta, void *stream);
+
+/* Evolve `steps` second-order steps (Eq. secondorder) on the grid's current
+ * state.  FP32 grids run the fused kernel: K whole steps per HBM round trip
+ * on TMA-staged shared-memory tiles (temporal blocking; K = 0 picks the
+ * depth automatically, 1 <= K <= 8 forces it; a remainder of steps % K runs
+ * at a smaller depth).  FP64 grids run the one-sweep-per-kernel path (K
+ * must be 0).  Async. */
+ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream);
+
+/* The plain path: one kernel per sweep (8 sweeps + the phase = 9 launches
+ * per step), in place, for FP32 or FP64 grids.  The reference point the
+ * fused path is measured against.  Async. */
+ts_status ts_evolve_plain(ts_grid *g, int64_t steps, void *stream);
+
+/* Observables of the current state, reduced on the device with FP64
+ * compensated (Neumaier) partial sums, finished on the device, copied back.
+ * Syncs `stream`. */
+typedef struct {
+    double norm;        /* sum |psi|^2 (Sec. 2: conserved by the unitary U) */
+    double x, y;        /* <x>, <y> = sum x|psi|^2 / norm, ...               */
+    double x2, y2;      /* <x^2>, <y^2>                                      */
+    double e_kin;       /* -J sum over neighbour pairs 2 Re(conj(psi_j) psi_k) */
+    double e_pot;       /* sum V |psi|^2                                     */
+} ts_observables;
+
+ts_status ts_observe(ts_grid *g, ts_observables *out, void *stream);
+ts_status ts_norm(ts_grid *g, double *out, void *stream);
+ts_status ts_expect_xy(ts_grid *g, double *x, double *y, void *stream);
+ts_status ts_energy(ts_grid *g, double *out, void *stream);   /* e_kin + e_pot */
+
+/* Evolve n independent grids (steps[i] steps each, fused depth K as in
+ * ts_evolve) on one stream.  Async. */
+ts_status ts_evolve_batched(ts_grid *const *g, int n, const int64_t *steps, int K,
+                            void *stream);
+
+/* Number of kernels this thread's calls enqueued since the last reset. */
+int64_t ts_launch_count(int reset);
+
+const char *ts_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TROTTER_H */

@@ -1,0 +1,516 @@
+// C ABI of libtrotter.so (declared in include/trotter.h).
+//
+// Host-side only: argument checks, the slab layout, staging of host input
+// through the grid's own ping-pong planes, kernel dispatch and error
+// reporting.  Every step of the method runs in the kernels of plain.cu,
+// fused.cu and reduce.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/trotter.h"
+#include "internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+thread_local int64_t g_launches = 0;
+
+ts_status fail(ts_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+ts_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(TS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr int64_t kMaxSide = int64_t(1) << 20;
+constexpr int kPlanes = 7;   // re_a, im_a, re_b, im_b, gamma_V, s_V, V
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t scratch_bytes()
+{
+    // partials, result, error word
+    return round_up(sizeof(double) * ts::OBS_MAX_BLOCKS * ts::OBS_Q, 256) +
+           round_up(sizeof(double) * ts::OBS_Q, 256) + 256;
+}
+
+}  // namespace
+
+struct ts_grid {
+    ts_layout L;
+    size_t esize;
+    unsigned char *slab;
+    bool owns_slab;
+    int cur;                 // 0: planes 0/1 hold the state, 1: planes 2/3
+    double dt, theta, J;
+    double g1, s1, g2, s2;   // rotation at theta and 2 theta, versine form, FP64
+    double *partials, *result;
+    int *err;
+    bool tmaps_ok;
+    CUtensorMap tm_re[2], tm_im[2], tm_pg, tm_ps;
+
+    void *plane(int i) const { return slab + (size_t)i * L.plane_bytes; }
+    void *re() const { return plane(2 * cur); }
+    void *im() const { return plane(2 * cur + 1); }
+    void *re_other() const { return plane(2 * (cur ^ 1)); }
+    void *im_other() const { return plane(2 * (cur ^ 1) + 1); }
+    void *pg() const { return plane(4); }
+    void *ps() const { return plane(5); }
+    void *vp() const { return plane(6); }
+    bool f64() const { return L.dtype == TS_F64; }
+};
+
+namespace ts {
+void count_launches(int64_t n) { g_launches += n; }
+}  // namespace ts
+
+extern "C" {
+
+const char *ts_last_error(void) { return g_err; }
+
+int64_t ts_launch_count(int reset)
+{
+    int64_t v = g_launches;
+    if (reset) g_launches = 0;
+    return v;
+}
+
+ts_status ts_grid_layout(int64_t nx, int64_t ny, ts_dtype dtype, ts_layout *out)
+{
+    if (!out) return fail(TS_ERR_ARG, "ts_grid_layout: out is NULL");
+    if (nx < 1 || ny < 1 || nx > kMaxSide || ny > kMaxSide)
+        return fail(TS_ERR_ARG, "ts_grid_layout: sides must be in [1, 2^20], got %lld x %lld",
+                    (long long)nx, (long long)ny);
+    if (dtype != TS_F32 && dtype != TS_F64)
+        return fail(TS_ERR_ARG, "ts_grid_layout: unknown dtype %d", (int)dtype);
+    const size_t es = dtype == TS_F64 ? 8 : 4;
+    out->nx = nx;
+    out->ny = ny;
+    out->pitch = (int64_t)round_up((size_t)nx, 32);
+    out->plane_bytes = round_up((size_t)out->pitch * (size_t)ny * es, 256);
+    out->slab_bytes = kPlanes * out->plane_bytes + scratch_bytes();
+    out->dtype = dtype;
+    return TS_OK;
+}
+
+ts_status ts_create_grid(int64_t nx, int64_t ny, ts_dtype dtype, void *slab, size_t slab_bytes,
+                         ts_grid **out)
+{
+    if (!out) return fail(TS_ERR_ARG, "ts_create_grid: out is NULL");
+    *out = nullptr;
+    ts_layout L;
+    ts_status st = ts_grid_layout(nx, ny, dtype, &L);
+    if (st != TS_OK) return st;
+    if (slab) {
+        if (((uintptr_t)slab & 255u) != 0)
+            return fail(TS_ERR_ARG, "ts_create_grid: slab must be 256-byte aligned");
+        if (slab_bytes < L.slab_bytes)
+            return fail(TS_ERR_ARG, "ts_create_grid: slab has %zu bytes, needs %zu", slab_bytes,
+                        L.slab_bytes);
+    }
+    ts_grid *g = new (std::nothrow) ts_grid();
+    if (!g) return fail(TS_ERR_OOM, "ts_create_grid: host allocation failed");
+    g->L = L;
+    g->esize = dtype == TS_F64 ? 8 : 4;
+    g->owns_slab = slab == nullptr;
+    if (g->owns_slab) {
+        cudaError_t e = cudaMalloc((void **)&g->slab, L.slab_bytes);
+        if (e != cudaSuccess) {
+            delete g;
+            cudaGetLastError();
+            return fail(TS_ERR_OOM, "ts_create_grid: cudaMalloc(%zu): %s", L.slab_bytes,
+                        cudaGetErrorString(e));
+        }
+    } else {
+        g->slab = (unsigned char *)slab;
+    }
+    cudaError_t e = cudaMemset(g->slab, 0, L.slab_bytes);
+    if (e != cudaSuccess) {
+        if (g->owns_slab) cudaFree(g->slab);
+        delete g;
+        return cuda_fail(e, "ts_create_grid: zero-fill");
+    }
+    unsigned char *scr = g->slab + kPlanes * L.plane_bytes;
+    g->partials = (double *)scr;
+    scr += round_up(sizeof(double) * ts::OBS_MAX_BLOCKS * ts::OBS_Q, 256);
+    g->result = (double *)scr;
+    scr += round_up(sizeof(double) * ts::OBS_Q, 256);
+    g->err = (int *)scr;
+    g->cur = 0;
+    g->dt = g->theta = g->J = 0.0;
+    g->g1 = g->s1 = g->g2 = g->s2 = 0.0;
+    g->tmaps_ok = false;
+    if (dtype == TS_F32) {
+        const char *why = "";
+        bool ok = true;
+        for (int c = 0; c < 2 && ok; ++c) {
+            ok = ts::make_plane_tensor_map(&g->tm_re[c], g->plane(2 * c), (int)nx, (int)ny,
+                                           L.pitch, &why) &&
+                 ts::make_plane_tensor_map(&g->tm_im[c], g->plane(2 * c + 1), (int)nx, (int)ny,
+                                           L.pitch, &why);
+        }
+        ok = ok && ts::make_plane_tensor_map(&g->tm_pg, g->pg(), (int)nx, (int)ny, L.pitch, &why) &&
+             ts::make_plane_tensor_map(&g->tm_ps, g->ps(), (int)nx, (int)ny, L.pitch, &why);
+        if (!ok) {
+            if (g->owns_slab) cudaFree(g->slab);
+            delete g;
+            return fail(TS_ERR_CUDA, "ts_create_grid: %s", why);
+        }
+        g->tmaps_ok = true;
+    }
+    *out = g;
+    return TS_OK;
+}
+
+ts_status ts_destroy_grid(ts_grid *g)
+{
+    if (!g) return TS_OK;
+    cudaError_t e = cudaSuccess;
+    if (g->owns_slab) e = cudaFree(g->slab);
+    delete g;
+    if (e != cudaSuccess) return cuda_fail(e, "ts_destroy_grid: cudaFree");
+    return TS_OK;
+}
+
+ts_status ts_grid_info(const ts_grid *g, ts_layout *layout, void **re, void **im)
+{
+    if (!g) return fail(TS_ERR_ARG, "ts_grid_info: grid is NULL");
+    if (layout) *layout = g->L;
+    if (re) *re = g->re();
+    if (im) *im = g->im();
+    return TS_OK;
+}
+
+namespace {
+
+// Copy a dense host array into the staging region (the two non-current
+// planes, contiguous in the slab) and convert it into `dst` on the device.
+ts_status stage_in(ts_grid *g, const void *host, ts_dtype src_dtype, void *dst, cudaStream_t st)
+{
+    const size_t n = (size_t)g->L.nx * (size_t)g->L.ny;
+    const size_t es = src_dtype == TS_F64 ? 8 : 4;
+    if (n * es > 2 * g->L.plane_bytes)
+        return fail(TS_ERR_ARG, "staging region too small");  // cannot happen by layout
+    void *stage = g->re_other();
+    cudaError_t e = cudaMemcpyAsync(stage, host, n * es, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    e = ts::launch_convert_in(stage, src_dtype == TS_F64, dst, g->f64(), (int)g->L.nx,
+                              (int)g->L.ny, g->L.pitch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "convert kernel");
+    return TS_OK;
+}
+
+ts_status check_errword(ts_grid *g, cudaStream_t st)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel error (reported at sync)");
+    if (h != 0) {
+        cudaMemsetAsync(g->err, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        if (h & ts::ERRBIT_WAIT_TIMEOUT)
+            return fail(TS_ERR_TIMEOUT, "a bounded wait in a fused kernel gave up (error word %d)", h);
+        return fail(TS_ERR_CUDA, "a kernel reported error word %d", h);
+    }
+    return TS_OK;
+}
+
+}  // namespace
+
+ts_status ts_set_state(ts_grid *g, const void *re, const void *im, ts_dtype src_dtype,
+                       ts_mem where, void *stream)
+{
+    if (!g || !re || !im) return fail(TS_ERR_ARG, "ts_set_state: null argument");
+    if (src_dtype != TS_F32 && src_dtype != TS_F64)
+        return fail(TS_ERR_ARG, "ts_set_state: unknown dtype");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool sf = src_dtype == TS_F64;
+    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    if (where == TS_DEVICE) {
+        cudaError_t e = ts::launch_convert_in(re, sf, g->re(), g->f64(), nx, ny, g->L.pitch, st);
+        if (e == cudaSuccess)
+            e = ts::launch_convert_in(im, sf, g->im(), g->f64(), nx, ny, g->L.pitch, st);
+        if (e != cudaSuccess) return cuda_fail(e, "ts_set_state: convert kernel");
+        return TS_OK;
+    }
+    if (where != TS_HOST) return fail(TS_ERR_ARG, "ts_set_state: unknown memory kind");
+    if (sf == g->f64()) {
+        // same type: straight pitched copies
+        const size_t es = g->esize;
+        cudaError_t e = cudaMemcpy2DAsync(g->re(), g->L.pitch * es, re, nx * es, nx * es, ny,
+                                          cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(g->im(), g->L.pitch * es, im, nx * es, nx * es, ny,
+                                  cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "ts_set_state: host-to-device copy");
+        return TS_OK;
+    }
+    ts_status s = stage_in(g, re, src_dtype, g->re(), st);
+    if (s != TS_OK) return s;
+    cudaError_t e = cudaStreamSynchronize(st);   // staging region is reused next
+    if (e != cudaSuccess) return cuda_fail(e, "ts_set_state");
+    s = stage_in(g, im, src_dtype, g->im(), st);
+    if (s != TS_OK) return s;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "ts_set_state");
+    return TS_OK;
+}
+
+ts_status ts_get_state(ts_grid *g, void *re, void *im, ts_dtype dst_dtype, ts_mem where,
+                       void *stream)
+{
+    if (!g || !re || !im) return fail(TS_ERR_ARG, "ts_get_state: null argument");
+    if (dst_dtype != TS_F32 && dst_dtype != TS_F64)
+        return fail(TS_ERR_ARG, "ts_get_state: unknown dtype");
+    cudaStream_t st = (cudaStream_t)stream;
+    ts_status s = check_errword(g, st);
+    if (s != TS_OK) return s;
+    const bool df = dst_dtype == TS_F64;
+    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    const size_t n = (size_t)nx * ny;
+    cudaError_t e;
+    if (where == TS_DEVICE) {
+        e = ts::launch_convert_out(g->re(), g->f64(), re, df, nx, ny, g->L.pitch, st);
+        if (e == cudaSuccess)
+            e = ts::launch_convert_out(g->im(), g->f64(), im, df, nx, ny, g->L.pitch, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "ts_get_state");
+        return TS_OK;
+    }
+    if (where != TS_HOST) return fail(TS_ERR_ARG, "ts_get_state: unknown memory kind");
+    if (df == g->f64()) {
+        const size_t es = g->esize;
+        e = cudaMemcpy2DAsync(re, nx * es, g->re(), g->L.pitch * es, nx * es, ny,
+                              cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(im, nx * es, g->im(), g->L.pitch * es, nx * es, ny,
+                                  cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "ts_get_state: device-to-host copy");
+        return TS_OK;
+    }
+    // convert on the device into the staging region, then copy out
+    const size_t es = df ? 8 : 4;
+    void *stage = g->re_other();
+    void *dsts[2] = {re, im};
+    void *srcs[2] = {g->re(), g->im()};
+    for (int c = 0; c < 2; ++c) {
+        e = ts::launch_convert_out(srcs[c], g->f64(), stage, df, nx, ny, g->L.pitch, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dsts[c], stage, n * es, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "ts_get_state");
+    }
+    return TS_OK;
+}
+
+ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt, double theta,
+                           void *stream)
+{
+    if (!g) return fail(TS_ERR_ARG, "ts_set_potential: grid is NULL");
+    if (!std::isfinite(dt) || !std::isfinite(theta))
+        return fail(TS_ERR_ARG, "ts_set_potential: dt and theta must be finite");
+    if (where != TS_HOST && where != TS_DEVICE)
+        return fail(TS_ERR_ARG, "ts_set_potential: unknown memory kind");
+    cudaStream_t st = (cudaStream_t)stream;
+    g->dt = dt;
+    g->theta = theta;
+    g->J = dt != 0.0 ? 2.0 * theta / dt : 0.0;
+    // kinetic rotation in versine form, FP64, rounded once where used
+    const double sh1 = std::sin(0.5 * theta), sh2 = std::sin(theta);
+    g->g1 = 2.0 * sh1 * sh1;
+    g->s1 = std::sin(theta);
+    g->g2 = 2.0 * sh2 * sh2;
+    g->s2 = std::sin(2.0 * theta);
+    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    cudaError_t e;
+    if (!V) {
+        e = cudaMemsetAsync(g->pg(), 0, 3 * g->L.plane_bytes, st);   // planes 4, 5, 6
+        if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: clear");
+        return TS_OK;
+    }
+    const double *src = V;
+    if (where == TS_HOST) {
+        const size_t n = (size_t)nx * ny;
+        e = cudaMemcpyAsync(g->re_other(), V, n * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: host-to-device copy");
+        src = (const double *)g->re_other();
+    }
+    e = ts::launch_phase_table(src, g->pg(), g->ps(), g->vp(), g->f64(), nx, ny, g->L.pitch, dt,
+                               st);
+    if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: table kernel");
+    if (where == TS_HOST) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential");
+    }
+    return TS_OK;
+}
+
+namespace {
+
+ts_status plain_steps(ts_grid *g, int64_t steps, cudaStream_t st)
+{
+    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    const int64_t pitch = g->L.pitch;
+    void *re = g->re(), *im = g->im();
+    const bool f = g->f64();
+    double gg = g->g1, ss = g->s1;
+    if (!f) {   // FP32 path: coefficients rounded once to float
+        gg = (double)(float)gg;
+        ss = (double)(float)ss;
+    }
+    for (int64_t n = 0; n < steps; ++n) {
+        cudaError_t e = cudaSuccess;
+        const int seq_axis[4] = {0, 0, 1, 1}, seq_par[4] = {0, 1, 0, 1};
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+            e = ts::launch_plain_sweep(re, im, f, nx, ny, pitch, seq_axis[i], seq_par[i], gg, ss, st);
+        if (e == cudaSuccess)
+            e = ts::launch_plain_phase(re, im, g->pg(), g->ps(), f, nx, ny, pitch, st);
+        for (int i = 3; i >= 0 && e == cudaSuccess; --i)
+            e = ts::launch_plain_sweep(re, im, f, nx, ny, pitch, seq_axis[i], seq_par[i], gg, ss, st);
+        if (e != cudaSuccess) return cuda_fail(e, "plain sweep launch");
+    }
+    return TS_OK;
+}
+
+int auto_depth() { return 4; }
+
+ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
+{
+    if (!g->tmaps_ok) return fail(TS_ERR_STATE, "fused path: tensor maps missing");
+    int64_t left = steps;
+    while (left > 0) {
+        const int k = (int)(left >= K ? K : left);
+        ts::FusedLaunch a;
+        a.tm_re = &g->tm_re[g->cur];
+        a.tm_im = &g->tm_im[g->cur];
+        a.tm_pg = &g->tm_pg;
+        a.tm_ps = &g->tm_ps;
+        a.out_re = (float *)g->re_other();
+        a.out_im = (float *)g->im_other();
+        a.nx = (int)g->L.nx;
+        a.ny = (int)g->L.ny;
+        a.pitch = g->L.pitch;
+        a.g1 = (float)g->g1;
+        a.s1 = (float)g->s1;
+        a.g2 = (float)g->g2;
+        a.s2 = (float)g->s2;
+        a.err = g->err;
+        cudaError_t e = ts::launch_fused(k, a, st);
+        if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+        g->cur ^= 1;
+        left -= k;
+    }
+    return TS_OK;
+}
+
+}  // namespace
+
+ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
+{
+    if (!g) return fail(TS_ERR_ARG, "ts_evolve: grid is NULL");
+    if (steps < 0) return fail(TS_ERR_ARG, "ts_evolve: negative step count");
+    if (K < 0 || K > ts::FUSED_MAX_K) return fail(TS_ERR_ARG, "ts_evolve: K must be in [0, 8]");
+    if (steps == 0) return TS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (g->f64()) {
+        if (K != 0)
+            return fail(TS_ERR_UNSUPPORTED, "ts_evolve: FP64 grids run the plain path (K must be 0)");
+        return plain_steps(g, steps, st);
+    }
+    return fused_steps(g, steps, K == 0 ? auto_depth() : K, st);
+}
+
+ts_status ts_evolve_plain(ts_grid *g, int64_t steps, void *stream)
+{
+    if (!g) return fail(TS_ERR_ARG, "ts_evolve_plain: grid is NULL");
+    if (steps < 0) return fail(TS_ERR_ARG, "ts_evolve_plain: negative step count");
+    return plain_steps(g, steps, (cudaStream_t)stream);
+}
+
+ts_status ts_evolve_batched(ts_grid *const *gs, int n, const int64_t *steps, int K, void *stream)
+{
+    if (n < 0 || (n > 0 && (!gs || !steps))) return fail(TS_ERR_ARG, "ts_evolve_batched: bad arguments");
+    for (int i = 0; i < n; ++i) {
+        ts_status s = ts_evolve(gs[i], steps[i], K, stream);
+        if (s != TS_OK) return s;
+    }
+    return TS_OK;
+}
+
+namespace {
+
+ts_status observe(ts_grid *g, bool norm_only, double *res, cudaStream_t st)
+{
+    cudaError_t e = ts::launch_observe(g->re(), g->im(), g->vp(), g->f64(), (int)g->L.nx,
+                                       (int)g->L.ny, g->L.pitch, g->J, norm_only, g->partials,
+                                       g->result, st);
+    if (e != cudaSuccess) return cuda_fail(e, "observables kernel");
+    e = cudaMemcpyAsync(res, g->result, sizeof(double) * ts::OBS_Q, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "observables copy");
+    return check_errword(g, st);
+}
+
+}  // namespace
+
+ts_status ts_observe(ts_grid *g, ts_observables *out, void *stream)
+{
+    if (!g || !out) return fail(TS_ERR_ARG, "ts_observe: null argument");
+    double r[ts::OBS_Q];
+    ts_status s = observe(g, false, r, (cudaStream_t)stream);
+    if (s != TS_OK) return s;
+    out->norm = r[0];
+    const double inv = r[0] != 0.0 ? 1.0 / r[0] : 0.0;
+    out->x = r[1] * inv;
+    out->y = r[2] * inv;
+    out->x2 = r[3] * inv;
+    out->y2 = r[4] * inv;
+    out->e_kin = r[5];
+    out->e_pot = r[6];
+    return TS_OK;
+}
+
+ts_status ts_norm(ts_grid *g, double *out, void *stream)
+{
+    if (!g || !out) return fail(TS_ERR_ARG, "ts_norm: null argument");
+    double r[ts::OBS_Q];
+    ts_status s = observe(g, true, r, (cudaStream_t)stream);
+    if (s != TS_OK) return s;
+    *out = r[0];
+    return TS_OK;
+}
+
+ts_status ts_expect_xy(ts_grid *g, double *x, double *y, void *stream)
+{
+    if (!g || !x || !y) return fail(TS_ERR_ARG, "ts_expect_xy: null argument");
+    ts_observables o;
+    ts_status s = ts_observe(g, &o, stream);
+    if (s != TS_OK) return s;
+    *x = o.x;
+    *y = o.y;
+    return TS_OK;
+}
+
+ts_status ts_energy(ts_grid *g, double *out, void *stream)
+{
+    if (!g || !out) return fail(TS_ERR_ARG, "ts_energy: null argument");
+    ts_observables o;
+    ts_status s = ts_observe(g, &o, stream);
+    if (s != TS_OK) return s;
+    *out = o.e_kin + o.e_pot;
+    return TS_OK;
+}
+
+}  // extern "C"

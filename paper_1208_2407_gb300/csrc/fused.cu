@@ -1,0 +1,511 @@
+// Fused, temporally blocked second-order Trotter-Suzuki steps (FP32).
+//
+// One launch applies K whole steps U2(dt) (Sec. 2, Eq. secondorder) per HBM
+// round trip: it reads the state (re, im) and the potential-phase table
+// (gamma_V, s_V) once and writes the state once, 24 B per site, for K steps.
+//
+// Operator order.  One step applies X-even, X-odd, Y-even, Y-odd (half angle
+// theta), the phase exp(-i V dt), then Y-odd, Y-even, X-odd, X-even.  X
+// sweeps act on rows and Y sweeps on columns, so every X factor commutes with
+// every Y factor.  Between two consecutive phases the factors
+//   Yo Ye Xo Xe | Xe Xo Ye Yo   therefore equal   [Xo Xe(2t) Xo] [Yo Ye(2t) Yo]
+// (Xe(t) Xe(t) = Xe(2t) exactly: the same disjoint pair rotations), so K steps
+// take 6K + 2 sweeps instead of 8K.  The results equal the literal product up
+// to FP32 rounding.
+//
+// Geometry ("warp streams").  A warp owns a strip of 128 columns (lane l
+// holds columns 4l..4l+3 of a row in registers as float4 re/im) and walks
+// down a range of rows.  Row pairs arrive through a ring of shared-memory
+// slots that TMA (cp.async.bulk.tensor.2d, 128 x 2 boxes of each of the four
+// planes) fills ahead of use; an mbarrier per slot tracks each fill.
+//  - X sweeps are row-local: pairs inside a lane's float4 rotate in
+//    registers, the pair that straddles two lanes uses warp shuffles.  The
+//    strip reads h = roundup(2K, 4) halo columns per side (the valid region
+//    shrinks by 2 columns per side per step) and stores the inner 128 - 2h.
+//  - Y sweeps couple consecutive rows held by the same lane.  The K steps form
+//    a software pipeline down the rows: an even-family sweep on a row pair
+//    that starts at an even row, or an odd-family one on a pair that starts
+//    at an odd row, is "aligned" and completes at once; the other kind waits
+//    for the next row and carries one row in registers.  The output trails
+//    the input by 2K rows; a row range reads 2K halo rows above and below.
+//  - The phase of step k is read from the slot ring where its rows still sit
+//    (the ring keeps K slots behind the current one).
+// Grid-edge sites: TMA fills rows/columns outside the grid with zeros, and a
+// pair whose partner lies outside the grid gets coefficients (0, 0), i.e. the
+// identity (open boundaries: the unpaired site is unchanged).
+//
+// Work split: a persistent launch of P warps; the (strip, row-pair) units
+// are cut into P equal contiguous ranges, so all warps finish together.
+//
+// Every wait on an mbarrier is bounded (globaltimer): on a timeout the warp
+// sets an error bit, waits (bounded) for its own outstanding copies and
+// returns; the host reports TS_ERR_TIMEOUT at its next synchronising call.
+#include <cstdio>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ts {
+
+namespace {
+
+constexpr int WARPS_PER_CTA = 4;
+constexpr int PREFETCH = 2;                          // D: slots in flight beyond the ring's tail
+constexpr int PLANE_SLOT_BYTES = FUSED_BOX_ROWS * FUSED_BOX_COLS * 4;   // 1 KiB
+constexpr int SLOT_BYTES = 4 * PLANE_SLOT_BYTES;                        // re, im, g_V, s_V
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;    // 2 s per wait
+constexpr uint32_t FULL = 0xffffffffu;
+
+template <int K>
+struct Cfg {
+    static constexpr int NS = PREFETCH + K + 1;      // ring slots per warp
+    static constexpr int HALO = ((2 * K + 3) / 4) * 4;
+    static constexpr int VALID = FUSED_BOX_COLS - 2 * HALO;
+    static constexpr int SMEM = 1024 + WARPS_PER_CTA * NS * (SLOT_BYTES + 8);
+};
+
+struct Frag {
+    float4 re, im;
+};
+
+struct KParams {
+    float *out_re, *out_im;
+    int nx, ny;
+    int64_t pitch;
+    int n_strips, n_pairs;
+    int64_t units;
+    int total_warps;
+    float g1, s1, g2, s2;
+    int *err;
+};
+
+// ---- PTX wrappers ---------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; returns false after WAIT_LIMIT_NS without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---- register-level sweeps ------------------------------------------------
+struct XEven {
+    float g0, s0, g1, s1;   // pairs (c0,c1) and (c2,c3) of the lane's float4
+};
+struct XOdd {
+    float g0, s0;           // pair (c1,c2), inside the lane
+    float gR, sR;           // pair (c3, next lane's c0)
+    float gL, sL;           // pair (previous lane's c3, c0)
+};
+
+__device__ __forceinline__ void x_even(Frag &f, const XEven &c)
+{
+    rot2(f.re.x, f.im.x, f.re.y, f.im.y, c.g0, c.s0);
+    rot2(f.re.z, f.im.z, f.re.w, f.im.w, c.g1, c.s1);
+}
+
+__device__ __forceinline__ void x_odd(Frag &f, const XOdd &c)
+{
+    const float nr = __shfl_down_sync(FULL, f.re.x, 1);
+    const float ni = __shfl_down_sync(FULL, f.im.x, 1);
+    const float pr = __shfl_up_sync(FULL, f.re.w, 1);
+    const float pi = __shfl_up_sync(FULL, f.im.w, 1);
+    rot2(f.re.y, f.im.y, f.re.z, f.im.z, c.g0, c.s0);
+    rot1(f.re.w, f.im.w, nr, ni, c.gR, c.sR);
+    rot1(f.re.x, f.im.x, pr, pi, c.gL, c.sL);
+}
+
+// Y pair rotation of two rows (all four columns of the lane).
+__device__ __forceinline__ void y_pair(Frag &a, Frag &b, float g, float s)
+{
+    rot2(a.re.x, a.im.x, b.re.x, b.im.x, g, s);
+    rot2(a.re.y, a.im.y, b.re.y, b.im.y, g, s);
+    rot2(a.re.z, a.im.z, b.re.z, b.im.z, g, s);
+    rot2(a.re.w, a.im.w, b.re.w, b.im.w, g, s);
+}
+
+__device__ __forceinline__ void phase4(Frag &f, float4 g, float4 s)
+{
+    phase1(f.re.x, f.im.x, g.x, s.x);
+    phase1(f.re.y, f.im.y, g.y, s.y);
+    phase1(f.re.z, f.im.z, g.z, s.z);
+    phase1(f.re.w, f.im.w, g.w, s.w);
+}
+
+__device__ __forceinline__ Frag zero_frag()
+{
+    Frag f;
+    f.re = make_float4(0.f, 0.f, 0.f, 0.f);
+    f.im = f.re;
+    return f;
+}
+
+// Slot layout: [plane][row][128 floats], planes 0 re, 1 im, 2 g_V, 3 s_V.
+__device__ __forceinline__ float4 lds4(const unsigned char *slot, int plane, int row, int lane)
+{
+    return *reinterpret_cast<const float4 *>(slot + plane * PLANE_SLOT_BYTES +
+                                             row * (FUSED_BOX_COLS * 4) + lane * 16);
+}
+
+template <int K>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32)
+fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ CUtensorMap tm_im,
+             const __grid_constant__ CUtensorMap tm_pg, const __grid_constant__ CUtensorMap tm_ps,
+             const KParams p)
+{
+    using C = Cfg<K>;
+    constexpr int NS = C::NS, HALO = C::HALO, VALID = C::VALID;
+
+    extern __shared__ unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * WARPS_PER_CTA + warp;
+    if (gw >= p.total_warps) return;
+
+    // carve: barriers first, then 1 KiB-aligned slots
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + warp * NS;
+    const uint32_t base_addr = smem_addr(smem_raw);
+    const uint32_t slots_off =
+        ((base_addr + WARPS_PER_CTA * NS * 8 + 1023u) & ~1023u) - base_addr;
+    unsigned char *ring = smem_raw + slots_off + (size_t)warp * NS * SLOT_BYTES;
+
+    if (lane == 0) {
+        for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    const int64_t u_begin = (int64_t)gw * p.units / p.total_warps;
+    const int64_t u_end = (int64_t)(gw + 1) * p.units / p.total_warps;
+    uint32_t seq = 0;       // pipeline slots issued (and consumed) by this warp so far
+    bool failed = false;
+
+    for (int64_t u = u_begin; u < u_end && !failed;) {
+        const int sx = (int)(u / p.n_pairs);
+        const int q0 = (int)(u - (int64_t)sx * p.n_pairs);
+        const int64_t q1_want = (int64_t)q0 + (u_end - u);
+        const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
+        u += q1 - q0;
+
+        const int XL = sx * VALID - HALO;              // first loaded column (multiple of 4)
+        const int xg = XL + 4 * lane;                  // this lane's first column
+        const int Y0 = 2 * q0, Y1 = 2 * q1;            // output rows [Y0, Y1)
+        const int Ys = Y0 - 2 * K;                     // first loaded row
+        const int n_iter = (Y1 - Y0) / 2 + 2 * K;      // row pairs loaded
+
+        // pair (x, x+1) is rotated iff both sites are on the grid
+        auto xok = [&](int x) { return x >= 0 && x + 1 < p.nx; };
+        const bool e0 = xok(xg), e1 = xok(xg + 2), o0 = xok(xg + 1), oR = xok(xg + 3),
+                   oL = xok(xg - 1);
+        const XEven E1 = {e0 ? p.g1 : 0.f, e0 ? p.s1 : 0.f, e1 ? p.g1 : 0.f, e1 ? p.s1 : 0.f};
+        const XEven E2 = {e0 ? p.g2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.g2 : 0.f, e1 ? p.s2 : 0.f};
+        const XOdd O = {o0 ? p.g1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
+                        oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
+        const bool store_lane =
+            lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
+
+        const uint32_t base = seq;
+        auto issue = [&](int j) {      // lane 0 only
+            const uint32_t q = base + (uint32_t)j;
+            unsigned char *slot = ring + (q % NS) * SLOT_BYTES;
+            uint64_t *bar = &bars[q % NS];
+            const int y = Ys + 2 * j;
+            mbar_expect_tx(bar, SLOT_BYTES);
+            tma_load_2d(slot + 0 * PLANE_SLOT_BYTES, &tm_re, XL, y, bar);
+            tma_load_2d(slot + 1 * PLANE_SLOT_BYTES, &tm_im, XL, y, bar);
+            tma_load_2d(slot + 2 * PLANE_SLOT_BYTES, &tm_pg, XL, y, bar);
+            tma_load_2d(slot + 3 * PLANE_SLOT_BYTES, &tm_ps, XL, y, bar);
+        };
+        const int n_pro = n_iter < NS ? n_iter : NS;
+        if (lane == 0) {
+            fence_proxy_async();
+            for (int j = 0; j < n_pro; ++j) issue(j);
+        }
+        int issued = n_pro;
+
+        auto slot_ptr = [&](int j) -> const unsigned char * {
+            return ring + ((base + (uint32_t)j) % NS) * SLOT_BYTES;
+        };
+        auto yok = [&](int y) { return y >= 0 && y + 1 < p.ny; };
+
+        Frag carry[2 * K];
+#pragma unroll
+        for (int i = 0; i < 2 * K; ++i) carry[i] = zero_frag();
+
+        for (int j = 0; j < n_iter; ++j) {
+            const uint32_t q = base + (uint32_t)j;
+            bool ok = mbar_wait(&bars[q % NS], (q / NS) & 1u, WAIT_LIMIT_NS);
+            ok = __all_sync(FULL, ok);
+            if (!ok) {
+                failed = true;
+                if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
+                // drain this warp's outstanding copies (bounded) before leaving
+                for (int jj = j + 1; jj < issued; ++jj) {
+                    const uint32_t qq = base + (uint32_t)jj;
+                    mbar_wait(&bars[qq % NS], (qq / NS) & 1u, WAIT_LIMIT_NS / 4);
+                }
+                mbar_wait(&bars[q % NS], (q / NS) & 1u, WAIT_LIMIT_NS / 4);
+                break;
+            }
+            const unsigned char *sj = slot_ptr(j);
+            Frag a, b;
+            a.re = lds4(sj, 0, 0, lane);
+            a.im = lds4(sj, 1, 0, lane);
+            b.re = lds4(sj, 0, 1, lane);
+            b.im = lds4(sj, 1, 1, lane);
+            const int yin = Ys + 2 * j;
+
+            // step 0, first half: Xe, Xo (row-local), Ye aligned, Yo shifted
+            x_even(a, E1);
+            x_even(b, E1);
+            x_odd(a, O);
+            x_odd(b, O);
+            {
+                const bool v = yok(yin);
+                y_pair(a, b, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+            }
+            {
+                const bool v = yok(yin - 1);
+                y_pair(carry[0], a, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+            }
+            Frag P = carry[0], Q = a;     // rows (yin-1, yin)
+            carry[0] = b;
+            int y1 = yin - 1;
+            // phase of step 0 on rows (y1, y1+1): slot j-1 row 1, slot j row 0
+            {
+                if (j >= 1) {
+                    const unsigned char *sp = slot_ptr(j - 1);
+                    phase4(P, lds4(sp, 2, 1, lane), lds4(sp, 3, 1, lane));
+                }
+                phase4(Q, lds4(sj, 2, 0, lane), lds4(sj, 3, 0, lane));
+            }
+#pragma unroll
+            for (int k = 1; k < K; ++k) {
+                {   // Yo (theta), aligned on (y1, y1+1), y1 odd
+                    const bool v = yok(y1);
+                    y_pair(P, Q, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+                }
+                // X group between two phases: Xo, Xe(2 theta), Xo
+                x_odd(P, O);
+                x_odd(Q, O);
+                x_even(P, E2);
+                x_even(Q, E2);
+                x_odd(P, O);
+                x_odd(Q, O);
+                {   // Ye (2 theta), shifted: pair (y1-1, y1)
+                    const bool v = yok(y1 - 1);
+                    y_pair(carry[2 * k - 1], P, v ? p.g2 : 0.f, v ? p.s2 : 0.f);
+                }
+                Frag P2 = carry[2 * k - 1], Q2 = P;   // rows (y1-1, y1)
+                carry[2 * k - 1] = Q;
+                {   // Yo (theta), shifted: pair (y1-2, y1-1)
+                    const bool v = yok(y1 - 2);
+                    y_pair(carry[2 * k], P2, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+                }
+                P = carry[2 * k];                     // rows (y1-2, y1-1)
+                carry[2 * k] = Q2;
+                Q = P2;
+                y1 -= 2;
+                // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
+                if (j - k - 1 >= 0) {
+                    const unsigned char *sp = slot_ptr(j - k - 1);
+                    phase4(P, lds4(sp, 2, 1, lane), lds4(sp, 3, 1, lane));
+                }
+                if (j - k >= 0) {
+                    const unsigned char *sq = slot_ptr(j - k);
+                    phase4(Q, lds4(sq, 2, 0, lane), lds4(sq, 3, 0, lane));
+                }
+            }
+            // last step, second half: Yo aligned, Ye shifted, Xo, Xe
+            {
+                const bool v = yok(y1);
+                y_pair(P, Q, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+            }
+            {
+                const bool v = yok(y1 - 1);
+                y_pair(carry[2 * K - 1], P, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+            }
+            Frag O0 = carry[2 * K - 1], O1 = P;      // rows (y1-1, y1)
+            carry[2 * K - 1] = Q;
+            x_odd(O0, O);
+            x_odd(O1, O);
+            x_even(O0, E1);
+            x_even(O1, E1);
+
+            const int yo = y1 - 1;                    // == yin - 2K
+            if (store_lane && yo >= Y0 && yo < Y1) {
+                float *r = p.out_re + (int64_t)yo * p.pitch + xg;
+                float *m = p.out_im + (int64_t)yo * p.pitch + xg;
+                if (yo < p.ny) {
+                    *reinterpret_cast<float4 *>(r) = O0.re;
+                    *reinterpret_cast<float4 *>(m) = O0.im;
+                }
+                if (yo + 1 < p.ny) {
+                    *reinterpret_cast<float4 *>(r + p.pitch) = O1.re;
+                    *reinterpret_cast<float4 *>(m + p.pitch) = O1.im;
+                }
+            }
+
+            // slot j-K is no longer read: refill its ring position
+            __syncwarp();
+            if (j >= K) {
+                const int jn = j - K + NS;
+                if (jn < n_iter) {
+                    if (lane == 0) {
+                        fence_proxy_async();
+                        issue(jn);
+                    }
+                    ++issued;
+                }
+            }
+        }
+        seq = base + (uint32_t)issued;
+        __syncwarp();
+    }
+}
+
+template <int K>
+cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
+{
+    using C = Cfg<K>;
+    static int blocks_per_sm = -1;
+    static int num_sms = 0;
+    if (blocks_per_sm < 0) {
+        cudaError_t e = cudaFuncSetAttribute(fused_kernel<K>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fused_kernel<K>,
+                                                          WARPS_PER_CTA * 32, C::SMEM);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    KParams p;
+    p.out_re = a.out_re;
+    p.out_im = a.out_im;
+    p.nx = a.nx;
+    p.ny = a.ny;
+    p.pitch = a.pitch;
+    p.n_strips = (a.nx + C::VALID - 1) / C::VALID;
+    p.n_pairs = (a.ny + 1) / 2;
+    p.units = (int64_t)p.n_strips * p.n_pairs;
+    // at least ~16 row pairs per warp, at most the resident warps
+    int64_t want = (p.units + 15) / 16;
+    int64_t cap = (int64_t)num_sms * blocks_per_sm * WARPS_PER_CTA;
+    p.total_warps = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    p.g1 = a.g1;
+    p.s1 = a.s1;
+    p.g2 = a.g2;
+    p.s2 = a.s2;
+    p.err = a.err;
+    const int blocks = (p.total_warps + WARPS_PER_CTA - 1) / WARPS_PER_CTA;
+    fused_kernel<K><<<blocks, WARPS_PER_CTA * 32, C::SMEM, st>>>(*a.tm_re, *a.tm_im, *a.tm_pg,
+                                                                  *a.tm_ps, p);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st)
+{
+    switch (K) {
+    case 1: return launch_k<1>(a, st);
+    case 2: return launch_k<2>(a, st);
+    case 3: return launch_k<3>(a, st);
+    case 4: return launch_k<4>(a, st);
+    case 5: return launch_k<5>(a, st);
+    case 6: return launch_k<6>(a, st);
+    case 7: return launch_k<7>(a, st);
+    case 8: return launch_k<8>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool make_plane_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
+                           const char **why)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult qr;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &qr) != cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess || !fn) {
+            *why = "cuTensorMapEncodeTiled is not available from the driver";
+            return false;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    cuuint64_t strides[1] = {(cuuint64_t)(pitch * 4)};
+    cuuint32_t box[2] = {FUSED_BOX_COLS, FUSED_BOX_ROWS};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *why = "cuTensorMapEncodeTiled rejected the plane layout";
+        return false;
+    }
+    return true;
+}
+
+}  // namespace ts

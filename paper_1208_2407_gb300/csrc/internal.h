@@ -1,0 +1,66 @@
+// Internal interface between the C-ABI layer (api.cu) and the kernel files.
+// Not installed; the public boundary is include/trotter.h.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace ts {
+
+// Error bits written by kernels into the grid's device error word.
+enum : int { ERRBIT_WAIT_TIMEOUT = 1, ERRBIT_BAD_CONFIG = 2 };
+
+// Number of FP64 quantities the observables reduction produces per block.
+constexpr int OBS_Q = 7;
+constexpr int OBS_MAX_BLOCKS = 1024;
+
+// --- conversions, tables, plain path (plain.cu) ---------------------------
+// dense (nx*ny, src type) -> pitched plane of dst type
+cudaError_t launch_convert_in(const void *src, bool src_f64, void *dst, bool dst_f64,
+                              int nx, int ny, int64_t pitch, cudaStream_t st);
+// pitched plane -> dense
+cudaError_t launch_convert_out(const void *src, bool src_f64, void *dst, bool dst_f64,
+                               int nx, int ny, int64_t pitch, cudaStream_t st);
+// V (dense FP64) -> (gamma_V, s_V, V) pitched planes of the grid's type
+cudaError_t launch_phase_table(const double *V, void *pg, void *ps, void *vplane, bool f64,
+                               int nx, int ny, int64_t pitch, double dt, cudaStream_t st);
+// one sweep along x (axis 0) or y (axis 1) of the given parity, in place
+cudaError_t launch_plain_sweep(void *re, void *im, bool f64, int nx, int ny, int64_t pitch,
+                               int axis, int parity, double g, double s, cudaStream_t st);
+// the diagonal phase exp(-i V dt) from the stored table, in place
+cudaError_t launch_plain_phase(void *re, void *im, const void *pg, const void *ps, bool f64,
+                               int nx, int ny, int64_t pitch, cudaStream_t st);
+
+// --- observables (reduce.cu) ----------------------------------------------
+// partials: OBS_MAX_BLOCKS * OBS_Q doubles; result: OBS_Q doubles.
+// norm_only computes only sum |psi|^2 (result[0]).
+cudaError_t launch_observe(const void *re, const void *im, const void *vplane, bool f64,
+                           int nx, int ny, int64_t pitch, double J, bool norm_only,
+                           double *partials, double *result, cudaStream_t st);
+
+// --- fused temporally blocked path (fused.cu) -----------------------------
+struct FusedLaunch {
+    const CUtensorMap *tm_re, *tm_im, *tm_pg, *tm_ps;   // host copies, by value at launch
+    float *out_re, *out_im;
+    int nx, ny;
+    int64_t pitch;
+    float g1, s1, g2, s2;    // rotation at theta and at 2 theta, versine form
+    int *err;
+};
+constexpr int FUSED_MAX_K = 8;
+constexpr int FUSED_BOX_COLS = 128;   // columns a warp strip loads (box width)
+constexpr int FUSED_BOX_ROWS = 2;     // rows per pipeline slot (box height)
+cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st);
+
+// Build a 2-D FP32 tensor map of an nx x ny pitched plane for the fused path.
+// Returns false (and a message) if the driver entry point is unavailable or
+// the encode call fails.
+bool make_plane_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
+                           const char **why);
+
+// Thread-local count of kernel launches issued by this library.
+void count_launches(int64_t n);
+
+}  // namespace ts

@@ -1,0 +1,319 @@
+"""Python binding of libtrotter.so (include/trotter.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; PyTorch supplies device
+memory (the grid slab) and the current CUDA stream.  The module-level
+functions carry the C names (``ts_create_grid``, ``ts_evolve``, ...) and take
+raw pointers; :class:`Grid` wraps them for numpy/torch arrays.
+
+If the library has not been built, the first call raises ``RuntimeError``:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtrotter.so")
+
+TS_OK, TS_ERR_ARG, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_BUSY, TS_ERR_TIMEOUT, TS_ERR_STATE, \
+    TS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+TS_F32, TS_F64 = 0, 1
+TS_HOST, TS_DEVICE = 0, 1
+
+STATUS_NAMES = {0: "TS_OK", -1: "TS_ERR_ARG", -2: "TS_ERR_OOM", -3: "TS_ERR_CUDA",
+                -4: "TS_ERR_BUSY", -5: "TS_ERR_TIMEOUT", -6: "TS_ERR_STATE",
+                -7: "TS_ERR_UNSUPPORTED"}
+
+
+class TrotterError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class ts_layout(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("pitch", ctypes.c_int64),
+                ("plane_bytes", ctypes.c_size_t), ("slab_bytes", ctypes.c_size_t),
+                ("dtype", ctypes.c_int)]
+
+
+class ts_observables(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("norm", "x", "y", "x2", "y2", "e_kin", "e_pot")]
+
+
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_INT = ctypes.c_int
+_DBL = ctypes.c_double
+
+_SIGNATURES = {
+    "ts_grid_layout": [_I64, _I64, _INT, ctypes.POINTER(ts_layout)],
+    "ts_create_grid": [_I64, _I64, _INT, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)],
+    "ts_destroy_grid": [_VP],
+    "ts_grid_info": [_VP, ctypes.POINTER(ts_layout), ctypes.POINTER(_VP), ctypes.POINTER(_VP)],
+    "ts_set_state": [_VP, _VP, _VP, _INT, _INT, _VP],
+    "ts_get_state": [_VP, _VP, _VP, _INT, _INT, _VP],
+    "ts_set_potential": [_VP, _VP, _INT, _DBL, _DBL, _VP],
+    "ts_evolve": [_VP, _I64, _INT, _VP],
+    "ts_evolve_plain": [_VP, _I64, _VP],
+    "ts_observe": [_VP, ctypes.POINTER(ts_observables), _VP],
+    "ts_norm": [_VP, ctypes.POINTER(_DBL), _VP],
+    "ts_expect_xy": [_VP, ctypes.POINTER(_DBL), ctypes.POINTER(_DBL), _VP],
+    "ts_energy": [_VP, ctypes.POINTER(_DBL), _VP],
+    "ts_evolve_batched": [ctypes.POINTER(_VP), _INT, ctypes.POINTER(_I64), _INT, _VP],
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load libtrotter.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtrotter.so is not built (%s); run "
+                               "`python -m paper_1208_2407_gb300.build`" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = _INT
+        lib.ts_last_error.argtypes = []
+        lib.ts_last_error.restype = ctypes.c_char_p
+        lib.ts_launch_count.argtypes = [_INT]
+        lib.ts_launch_count.restype = _I64
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    """Names the header declares, for the ABI test."""
+    return sorted(list(_SIGNATURES) + ["ts_last_error", "ts_launch_count"])
+
+
+def _check(status: int):
+    if status != TS_OK:
+        raise TrotterError(status, load().ts_last_error().decode(errors="replace"))
+
+
+def _call(name, *args):
+    _check(getattr(load(), name)(*args))
+
+
+# --- C-named wrappers (raw pointers / handles) ------------------------------
+def ts_grid_layout(nx: int, ny: int, dtype: int = TS_F32) -> ts_layout:
+    L = ts_layout()
+    _call("ts_grid_layout", nx, ny, dtype, ctypes.byref(L))
+    return L
+
+
+def ts_create_grid(nx, ny, dtype, slab_ptr, slab_bytes):
+    h = _VP()
+    _call("ts_create_grid", nx, ny, dtype, slab_ptr, slab_bytes, ctypes.byref(h))
+    return h
+
+
+def ts_destroy_grid(h):
+    _call("ts_destroy_grid", h)
+
+
+def ts_set_state(h, re_ptr, im_ptr, dtype, where, stream):
+    _call("ts_set_state", h, re_ptr, im_ptr, dtype, where, stream)
+
+
+def ts_get_state(h, re_ptr, im_ptr, dtype, where, stream):
+    _call("ts_get_state", h, re_ptr, im_ptr, dtype, where, stream)
+
+
+def ts_set_potential(h, v_ptr, where, dt, theta, stream):
+    _call("ts_set_potential", h, v_ptr, where, dt, theta, stream)
+
+
+def ts_evolve(h, steps, K, stream):
+    _call("ts_evolve", h, steps, K, stream)
+
+
+def ts_evolve_plain(h, steps, stream):
+    _call("ts_evolve_plain", h, steps, stream)
+
+
+def ts_observe(h, stream) -> ts_observables:
+    o = ts_observables()
+    _call("ts_observe", h, ctypes.byref(o), stream)
+    return o
+
+
+def ts_norm(h, stream) -> float:
+    v = _DBL()
+    _call("ts_norm", h, ctypes.byref(v), stream)
+    return v.value
+
+
+def ts_expect_xy(h, stream):
+    x, y = _DBL(), _DBL()
+    _call("ts_expect_xy", h, ctypes.byref(x), ctypes.byref(y), stream)
+    return x.value, y.value
+
+
+def ts_energy(h, stream) -> float:
+    v = _DBL()
+    _call("ts_energy", h, ctypes.byref(v), stream)
+    return v.value
+
+
+def ts_evolve_batched(handles, steps, K, stream):
+    n = len(handles)
+    arr = (_VP * n)(*[h.value if isinstance(h, _VP) else h for h in handles])
+    st = (_I64 * n)(*[int(s) for s in steps])
+    _call("ts_evolve_batched", arr, n, st, K, stream)
+
+
+def ts_launch_count(reset: bool = False) -> int:
+    return int(load().ts_launch_count(1 if reset else 0))
+
+
+def ts_last_error() -> str:
+    return load().ts_last_error().decode(errors="replace")
+
+
+# --- torch-facing convenience ----------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def current_stream_ptr():
+    torch = _torch()
+    return _VP(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype_code(dt) -> int:
+    name = str(dt)
+    if name.endswith("float64") or name in ("f64", "double"):
+        return TS_F64
+    if name.endswith("float32") or name in ("f32", "float"):
+        return TS_F32
+    raise ValueError("unsupported dtype %r" % (dt,))
+
+
+def _array_ptr(a, shape):
+    """(pointer, dtype code, where) for a numpy array or a torch tensor."""
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        if tuple(a.shape) != shape or not a.is_contiguous():
+            raise ValueError("expected a contiguous tensor of shape %s" % (shape,))
+        where = TS_DEVICE if a.is_cuda else TS_HOST
+        return _VP(a.data_ptr()), _dtype_code(a.dtype), where, a
+    arr = np.ascontiguousarray(a)
+    if arr.dtype not in (np.float32, np.float64):
+        arr = arr.astype(np.float64)
+    if arr.shape != shape:
+        raise ValueError("expected an array of shape %s, got %s" % (shape, arr.shape))
+    return _VP(arr.ctypes.data), _dtype_code(arr.dtype), TS_HOST, arr
+
+
+class Grid:
+    """One lattice on the current CUDA device, with its slab owned by torch."""
+
+    def __init__(self, nx: int, ny: int, dtype: str = "f32"):
+        torch = _torch()
+        self.nx, self.ny = int(nx), int(ny)
+        self.dtype = TS_F64 if dtype in ("f64", "float64", np.float64) else TS_F32
+        self.layout = ts_grid_layout(self.nx, self.ny, self.dtype)
+        self.slab = torch.empty(int(self.layout.slab_bytes), dtype=torch.uint8, device="cuda")
+        self.handle = ts_create_grid(self.nx, self.ny, self.dtype, _VP(self.slab.data_ptr()),
+                                     int(self.layout.slab_bytes))
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+    def close(self):
+        if self.handle is not None:
+            ts_destroy_grid(self.handle)
+            self.handle = None
+            self.slab = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, re, im, stream=None):
+        rp, rd, rw, keep_r = _array_ptr(re, self.shape)
+        ip, idt, iw, keep_i = _array_ptr(im, self.shape)
+        if (rd, rw) != (idt, iw):
+            raise ValueError("re and im must share dtype and memory kind")
+        ts_set_state(self.handle, rp, ip, rd, rw, stream or current_stream_ptr())
+        del keep_r, keep_i
+
+    def get_state(self, dtype=np.float64, device: bool = False, stream=None):
+        torch = _torch()
+        code = _dtype_code(np.dtype(dtype))
+        if device:
+            tdt = torch.float64 if code == TS_F64 else torch.float32
+            re = torch.empty(self.shape, dtype=tdt, device="cuda")
+            im = torch.empty(self.shape, dtype=tdt, device="cuda")
+            ts_get_state(self.handle, _VP(re.data_ptr()), _VP(im.data_ptr()), code, TS_DEVICE,
+                         stream or current_stream_ptr())
+            return re, im
+        re = np.empty(self.shape, dtype=np.float64 if code == TS_F64 else np.float32)
+        im = np.empty_like(re)
+        ts_get_state(self.handle, _VP(re.ctypes.data), _VP(im.ctypes.data), code, TS_HOST,
+                     stream or current_stream_ptr())
+        return re, im
+
+    def set_potential(self, V, dt: float, theta: float, stream=None):
+        st = stream or current_stream_ptr()
+        if V is None:
+            ts_set_potential(self.handle, None, TS_HOST, float(dt), float(theta), st)
+            return
+        torch = _torch()
+        if isinstance(V, torch.Tensor):
+            if V.dtype != torch.float64 or tuple(V.shape) != self.shape or not V.is_contiguous():
+                raise ValueError("V must be a contiguous float64 tensor of the grid's shape")
+            where = TS_DEVICE if V.is_cuda else TS_HOST
+            ts_set_potential(self.handle, _VP(V.data_ptr()), where, float(dt), float(theta), st)
+            return
+        Va = np.ascontiguousarray(V, dtype=np.float64)
+        if Va.shape != self.shape:
+            raise ValueError("V must have the grid's shape")
+        ts_set_potential(self.handle, _VP(Va.ctypes.data), TS_HOST, float(dt), float(theta), st)
+
+    def evolve(self, steps: int, K: int = 0, stream=None):
+        ts_evolve(self.handle, int(steps), int(K), stream or current_stream_ptr())
+
+    def evolve_plain(self, steps: int, stream=None):
+        ts_evolve_plain(self.handle, int(steps), stream or current_stream_ptr())
+
+    def observe(self, stream=None) -> dict:
+        o = ts_observe(self.handle, stream or current_stream_ptr())
+        return {n: getattr(o, n) for n, _ in ts_observables._fields_}
+
+    def norm(self, stream=None) -> float:
+        return ts_norm(self.handle, stream or current_stream_ptr())
+
+    def expect_xy(self, stream=None):
+        return ts_expect_xy(self.handle, stream or current_stream_ptr())
+
+    def energy(self, stream=None) -> float:
+        return ts_energy(self.handle, stream or current_stream_ptr())
+
+    def state_planes(self):
+        """Device pointers of the current re/im planes and the row pitch."""
+        L = ts_layout()
+        re, im = _VP(), _VP()
+        _call("ts_grid_info", self.handle, ctypes.byref(L), ctypes.byref(re), ctypes.byref(im))
+        return re.value, im.value, int(L.pitch)
+
+
+def evolve_batched(grids, steps, K: int = 0, stream=None):
+    ts_evolve_batched([g.handle for g in grids], steps, K, stream or current_stream_ptr())
