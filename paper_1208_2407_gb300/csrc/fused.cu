@@ -50,19 +50,32 @@ namespace ts {
 
 namespace {
 
-constexpr int WARPS_PER_CTA = 4;
-constexpr int PREFETCH = 2;                          // D: slots in flight beyond the ring's tail
+#ifndef TS_FUSED_WARPS_PER_CTA
+#define TS_FUSED_WARPS_PER_CTA 2
+#endif
+#ifndef TS_FUSED_PREFETCH
+#define TS_FUSED_PREFETCH 2
+#endif
+constexpr int WARPS_PER_CTA = TS_FUSED_WARPS_PER_CTA;
+constexpr int PREFETCH = TS_FUSED_PREFETCH;          // D: row pairs in flight ahead of use
 constexpr int PLANE_SLOT_BYTES = FUSED_BOX_ROWS * FUSED_BOX_COLS * 4;   // 1 KiB
-constexpr int SLOT_BYTES = 4 * PLANE_SLOT_BYTES;                        // re, im, g_V, s_V
+constexpr int SLOT_BYTES = 2 * PLANE_SLOT_BYTES;     // one ring slot: two planes of 2 rows
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;    // 2 s per wait
 constexpr uint32_t FULL = 0xffffffffu;
 
+// Two rings per warp, both indexed by the row pair j (rows Ys + 2j, +1):
+//  - the state ring (re, im) is read once, when row pair j enters the
+//    pipeline, so it needs PREFETCH + 1 slots;
+//  - the phase ring (gamma_V, s_V) is read by the phase of every step, the
+//    last one K row pairs later, so it needs PREFETCH + K + 1 slots.
 template <int K>
 struct Cfg {
-    static constexpr int NS = PREFETCH + K + 1;      // ring slots per warp
+    static constexpr int NSS = PREFETCH + 1;
+    static constexpr int NSP = PREFETCH + K + 1;
     static constexpr int HALO = ((2 * K + 3) / 4) * 4;
     static constexpr int VALID = FUSED_BOX_COLS - 2 * HALO;
-    static constexpr int SMEM = 1024 + WARPS_PER_CTA * NS * (SLOT_BYTES + 8);
+    static constexpr int WARP_SMEM = (NSS + NSP) * SLOT_BYTES;
+    static constexpr int SMEM = 1024 + WARPS_PER_CTA * (WARP_SMEM + (NSS + NSP) * 8);
 };
 
 struct Frag {
@@ -195,7 +208,8 @@ __device__ __forceinline__ Frag zero_frag()
     return f;
 }
 
-// Slot layout: [plane][row][128 floats], planes 0 re, 1 im, 2 g_V, 3 s_V.
+// Slot layout: [plane][row][128 floats]; state slots hold (re, im), phase
+// slots hold (gamma_V, s_V).
 __device__ __forceinline__ float4 lds4(const unsigned char *slot, int plane, int row, int lane)
 {
     return *reinterpret_cast<const float4 *>(slot + plane * PLANE_SLOT_BYTES +
@@ -209,29 +223,31 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
              const KParams p)
 {
     using C = Cfg<K>;
-    constexpr int NS = C::NS, HALO = C::HALO, VALID = C::VALID;
+    constexpr int NSS = C::NSS, NSP = C::NSP, HALO = C::HALO, VALID = C::VALID;
 
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * WARPS_PER_CTA + warp;
     if (gw >= p.total_warps) return;
 
-    // carve: barriers first, then 1 KiB-aligned slots
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw) + warp * NS;
+    // carve: barriers first, then 1 KiB-aligned slots (state ring, phase ring)
+    uint64_t *bar_s = reinterpret_cast<uint64_t *>(smem_raw) + warp * (NSS + NSP);
+    uint64_t *bar_p = bar_s + NSS;
     const uint32_t base_addr = smem_addr(smem_raw);
     const uint32_t slots_off =
-        ((base_addr + WARPS_PER_CTA * NS * 8 + 1023u) & ~1023u) - base_addr;
-    unsigned char *ring = smem_raw + slots_off + (size_t)warp * NS * SLOT_BYTES;
+        ((base_addr + WARPS_PER_CTA * (NSS + NSP) * 8 + 1023u) & ~1023u) - base_addr;
+    unsigned char *ring_s = smem_raw + slots_off + (size_t)warp * C::WARP_SMEM;
+    unsigned char *ring_p = ring_s + NSS * SLOT_BYTES;
 
     if (lane == 0) {
-        for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
+        for (int i = 0; i < NSS + NSP; ++i) mbar_init(&bar_s[i], 1);
         fence_mbar_init();
     }
     __syncwarp();
 
     const int64_t u_begin = (int64_t)gw * p.units / p.total_warps;
     const int64_t u_end = (int64_t)(gw + 1) * p.units / p.total_warps;
-    uint32_t seq = 0;       // pipeline slots issued (and consumed) by this warp so far
+    uint32_t seq = 0;       // row pairs issued (and consumed) by this warp so far
     bool failed = false;
 
     for (int64_t u = u_begin; u < u_end && !failed;) {
@@ -259,26 +275,38 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
             lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
 
         const uint32_t base = seq;
-        auto issue = [&](int j) {      // lane 0 only
+        auto issue_state = [&](int j) {      // lane 0 only
             const uint32_t q = base + (uint32_t)j;
-            unsigned char *slot = ring + (q % NS) * SLOT_BYTES;
-            uint64_t *bar = &bars[q % NS];
-            const int y = Ys + 2 * j;
+            unsigned char *slot = ring_s + (q % NSS) * SLOT_BYTES;
+            uint64_t *bar = &bar_s[q % NSS];
             mbar_expect_tx(bar, SLOT_BYTES);
-            tma_load_2d(slot + 0 * PLANE_SLOT_BYTES, &tm_re, XL, y, bar);
-            tma_load_2d(slot + 1 * PLANE_SLOT_BYTES, &tm_im, XL, y, bar);
-            tma_load_2d(slot + 2 * PLANE_SLOT_BYTES, &tm_pg, XL, y, bar);
-            tma_load_2d(slot + 3 * PLANE_SLOT_BYTES, &tm_ps, XL, y, bar);
+            tma_load_2d(slot, &tm_re, XL, Ys + 2 * j, bar);
+            tma_load_2d(slot + PLANE_SLOT_BYTES, &tm_im, XL, Ys + 2 * j, bar);
         };
-        const int n_pro = n_iter < NS ? n_iter : NS;
+        auto issue_phase = [&](int j) {      // lane 0 only
+            const uint32_t q = base + (uint32_t)j;
+            unsigned char *slot = ring_p + (q % NSP) * SLOT_BYTES;
+            uint64_t *bar = &bar_p[q % NSP];
+            mbar_expect_tx(bar, SLOT_BYTES);
+            tma_load_2d(slot, &tm_pg, XL, Ys + 2 * j, bar);
+            tma_load_2d(slot + PLANE_SLOT_BYTES, &tm_ps, XL, Ys + 2 * j, bar);
+        };
+        const int n_pro_s = n_iter < NSS ? n_iter : NSS;
+        const int n_pro_p = n_iter < NSP ? n_iter : NSP;
         if (lane == 0) {
             fence_proxy_async();
-            for (int j = 0; j < n_pro; ++j) issue(j);
+            for (int j = 0; j < n_pro_p; ++j) {
+                if (j < n_pro_s) issue_state(j);
+                issue_phase(j);
+            }
         }
-        int issued = n_pro;
+        int issued_s = n_pro_s, issued_p = n_pro_p;
 
-        auto slot_ptr = [&](int j) -> const unsigned char * {
-            return ring + ((base + (uint32_t)j) % NS) * SLOT_BYTES;
+        auto state_slot = [&](int j) -> const unsigned char * {
+            return ring_s + ((base + (uint32_t)j) % NSS) * SLOT_BYTES;
+        };
+        auto phase_slot = [&](int j) -> const unsigned char * {
+            return ring_p + ((base + (uint32_t)j) % NSP) * SLOT_BYTES;
         };
         auto yok = [&](int y) { return y >= 0 && y + 1 < p.ny; };
 
@@ -288,20 +316,25 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
 
         for (int j = 0; j < n_iter; ++j) {
             const uint32_t q = base + (uint32_t)j;
-            bool ok = mbar_wait(&bars[q % NS], (q / NS) & 1u, WAIT_LIMIT_NS);
+            bool ok = mbar_wait(&bar_s[q % NSS], (q / NSS) & 1u, WAIT_LIMIT_NS) &&
+                      mbar_wait(&bar_p[q % NSP], (q / NSP) & 1u, WAIT_LIMIT_NS);
             ok = __all_sync(FULL, ok);
             if (!ok) {
                 failed = true;
                 if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
                 // drain this warp's outstanding copies (bounded) before leaving
-                for (int jj = j + 1; jj < issued; ++jj) {
+                for (int jj = j; jj < issued_s; ++jj) {
                     const uint32_t qq = base + (uint32_t)jj;
-                    mbar_wait(&bars[qq % NS], (qq / NS) & 1u, WAIT_LIMIT_NS / 4);
+                    mbar_wait(&bar_s[qq % NSS], (qq / NSS) & 1u, WAIT_LIMIT_NS / 4);
                 }
-                mbar_wait(&bars[q % NS], (q / NS) & 1u, WAIT_LIMIT_NS / 4);
+                for (int jj = j; jj < issued_p; ++jj) {
+                    const uint32_t qq = base + (uint32_t)jj;
+                    mbar_wait(&bar_p[qq % NSP], (qq / NSP) & 1u, WAIT_LIMIT_NS / 4);
+                }
                 break;
             }
-            const unsigned char *sj = slot_ptr(j);
+            const unsigned char *sj = state_slot(j);
+            const unsigned char *pj = phase_slot(j);
             Frag a, b;
             a.re = lds4(sj, 0, 0, lane);
             a.im = lds4(sj, 1, 0, lane);
@@ -328,10 +361,10 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
             // phase of step 0 on rows (y1, y1+1): slot j-1 row 1, slot j row 0
             {
                 if (j >= 1) {
-                    const unsigned char *sp = slot_ptr(j - 1);
-                    phase4(P, lds4(sp, 2, 1, lane), lds4(sp, 3, 1, lane));
+                    const unsigned char *sp = phase_slot(j - 1);
+                    phase4(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
                 }
-                phase4(Q, lds4(sj, 2, 0, lane), lds4(sj, 3, 0, lane));
+                phase4(Q, lds4(pj, 0, 0, lane), lds4(pj, 1, 0, lane));
             }
 #pragma unroll
             for (int k = 1; k < K; ++k) {
@@ -362,12 +395,12 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
                 y1 -= 2;
                 // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
                 if (j - k - 1 >= 0) {
-                    const unsigned char *sp = slot_ptr(j - k - 1);
-                    phase4(P, lds4(sp, 2, 1, lane), lds4(sp, 3, 1, lane));
+                    const unsigned char *sp = phase_slot(j - k - 1);
+                    phase4(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
                 }
                 if (j - k >= 0) {
-                    const unsigned char *sq = slot_ptr(j - k);
-                    phase4(Q, lds4(sq, 2, 0, lane), lds4(sq, 3, 0, lane));
+                    const unsigned char *sq = phase_slot(j - k);
+                    phase4(Q, lds4(sq, 0, 0, lane), lds4(sq, 1, 0, lane));
                 }
             }
             // last step, second half: Yo aligned, Ye shifted, Xo, Xe
@@ -400,20 +433,19 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
                 }
             }
 
-            // slot j-K is no longer read: refill its ring position
+            // state slot j and phase slot j-K are no longer read: refill them
             __syncwarp();
-            if (j >= K) {
-                const int jn = j - K + NS;
-                if (jn < n_iter) {
-                    if (lane == 0) {
-                        fence_proxy_async();
-                        issue(jn);
-                    }
-                    ++issued;
-                }
+            const int js = j + NSS, jp = j - K + NSP;
+            const bool more_s = js < n_iter, more_p = j >= K && jp < n_iter;
+            if (lane == 0 && (more_s || more_p)) {
+                fence_proxy_async();
+                if (more_s) issue_state(js);
+                if (more_p) issue_phase(jp);
             }
+            issued_s += more_s;
+            issued_p += more_p;
         }
-        seq = base + (uint32_t)issued;
+        seq = base + (uint32_t)n_iter;
         __syncwarp();
     }
 }
