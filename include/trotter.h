@@ -148,6 +148,34 @@ ts_status ts_energy(ts_grid *g, double *out, void *stream);   /* e_kin + e_pot *
 ts_status ts_evolve_batched(ts_grid *const *g, int n, const int64_t *steps, int K,
                             void *stream);
 
+/* Sum of |psi|^2 over a pitched device state, without allocating anything.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code that runs where the device memory is
+ * already fully reserved by another allocator (a framework's caching pool,
+ * a serving process with a fixed HBM budget), or a loop that must not take
+ * the synchronising, latency-unbounded path of a fresh allocation.  It makes
+ * no cudaMalloc/cudaFree call and calls no allocating library routine.
+ *
+ *   re, im  device planes of `dtype`, ny rows of `pitch` elements (pitch >= nx);
+ *   out     device pointer to one double that receives the sum (caller-owned);
+ *   stream  as elsewhere; the call is asynchronous.
+ *
+ * Scratch: the per-block partial sums live in one fixed array of
+ * ts_norm_noalloc_scratch_bytes() bytes (57,344) inside the library's device
+ * image; every GPU that loads the library holds it until the process exits.
+ * The reduction uses at most 1024 blocks, so any grid with sides in [1, 2^20]
+ * fits; other sides, pitch < nx, null pointers or an unknown dtype return
+ * TS_ERR_ARG with a message in ts_last_error().
+ * The first call on each device looks the array's device address up (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (on different
+ * streams, or from different threads) race and must be serialised by the
+ * caller.  Nothing in the array needs clearing between calls. */
+ts_status ts_norm_noalloc(const void *re, const void *im, ts_dtype dtype, int64_t nx,
+                          int64_t ny, int64_t pitch, double *out, void *stream);
+size_t ts_norm_noalloc_scratch_bytes(void);
+
 /* Number of kernels this thread's calls enqueued since the last reset. */
 int64_t ts_launch_count(int reset);
 

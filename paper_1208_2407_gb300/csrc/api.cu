@@ -72,6 +72,15 @@ struct ts_grid {
 
 namespace ts {
 void count_launches(int64_t n) { g_launches += n; }
+
+int set_error(int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return status;
+}
 }  // namespace ts
 
 extern "C" {

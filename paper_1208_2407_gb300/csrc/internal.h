@@ -63,4 +63,7 @@ bool make_plane_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, in
 // Thread-local count of kernel launches issued by this library.
 void count_launches(int64_t n);
 
+// Record a message for ts_last_error() and return `status` (api.cu).
+int set_error(int status, const char *fmt, ...);
+
 }  // namespace ts

@@ -65,6 +65,7 @@ _SIGNATURES = {
     "ts_expect_xy": [_VP, ctypes.POINTER(_DBL), ctypes.POINTER(_DBL), _VP],
     "ts_energy": [_VP, ctypes.POINTER(_DBL), _VP],
     "ts_evolve_batched": [ctypes.POINTER(_VP), _INT, ctypes.POINTER(_I64), _INT, _VP],
+    "ts_norm_noalloc": [_VP, _VP, _INT, _I64, _I64, _I64, _VP, _VP],
 }
 
 _lock = threading.Lock()
@@ -89,13 +90,16 @@ def load():
         lib.ts_last_error.restype = ctypes.c_char_p
         lib.ts_launch_count.argtypes = [_INT]
         lib.ts_launch_count.restype = _I64
+        lib.ts_norm_noalloc_scratch_bytes.argtypes = []
+        lib.ts_norm_noalloc_scratch_bytes.restype = ctypes.c_size_t
         _lib = lib
         return lib
 
 
 def exported_symbols():
     """Names the header declares, for the ABI test."""
-    return sorted(list(_SIGNATURES) + ["ts_last_error", "ts_launch_count"])
+    return sorted(list(_SIGNATURES) + ["ts_last_error", "ts_launch_count",
+                                        "ts_norm_noalloc_scratch_bytes"])
 
 
 def _check(status: int):
@@ -173,6 +177,16 @@ def ts_evolve_batched(handles, steps, K, stream):
     arr = (_VP * n)(*[h.value if isinstance(h, _VP) else h for h in handles])
     st = (_I64 * n)(*[int(s) for s in steps])
     _call("ts_evolve_batched", arr, n, st, K, stream)
+
+
+def ts_norm_noalloc(re_ptr, im_ptr, dtype, nx, ny, pitch, out_ptr, stream):
+    """Norm of a pitched device state into a caller-owned device double,
+    using the library's fixed scratch instead of any allocation."""
+    _call("ts_norm_noalloc", re_ptr, im_ptr, dtype, nx, ny, pitch, out_ptr, stream)
+
+
+def ts_norm_noalloc_scratch_bytes() -> int:
+    return int(load().ts_norm_noalloc_scratch_bytes())
 
 
 def ts_launch_count(reset: bool = False) -> int:
