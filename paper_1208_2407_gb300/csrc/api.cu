@@ -53,11 +53,11 @@ struct ts_grid {
     bool owns_slab;
     int cur;                 // 0: planes 0/1 hold the state, 1: planes 2/3
     double dt, theta, J;
-    double g1, s1, g2, s2;   // rotation at theta and 2 theta, versine form, FP64
+    double g1, s1, t1, s2, t2;   // rotation coefficients (FP64): theta and 2 theta
     double *partials, *result;
     int *err;
     bool tmaps_ok;
-    CUtensorMap tm_re[2], tm_im[2], tm_pg, tm_ps;
+    CUtensorMap tm_state[2], tm_phase;   // (re, im) of pair 0 / 1; (gamma_V, s_V)
 
     void *plane(int i) const { return slab + (size_t)i * L.plane_bytes; }
     void *re() const { return plane(2 * cur); }
@@ -157,19 +157,16 @@ ts_status ts_create_grid(int64_t nx, int64_t ny, ts_dtype dtype, void *slab, siz
     g->err = (int *)scr;
     g->cur = 0;
     g->dt = g->theta = g->J = 0.0;
-    g->g1 = g->s1 = g->g2 = g->s2 = 0.0;
+    g->g1 = g->s1 = g->t1 = g->s2 = g->t2 = 0.0;
     g->tmaps_ok = false;
     if (dtype == TS_F32) {
         const char *why = "";
         bool ok = true;
-        for (int c = 0; c < 2 && ok; ++c) {
-            ok = ts::make_plane_tensor_map(&g->tm_re[c], g->plane(2 * c), (int)nx, (int)ny,
-                                           L.pitch, &why) &&
-                 ts::make_plane_tensor_map(&g->tm_im[c], g->plane(2 * c + 1), (int)nx, (int)ny,
-                                           L.pitch, &why);
-        }
-        ok = ok && ts::make_plane_tensor_map(&g->tm_pg, g->pg(), (int)nx, (int)ny, L.pitch, &why) &&
-             ts::make_plane_tensor_map(&g->tm_ps, g->ps(), (int)nx, (int)ny, L.pitch, &why);
+        for (int c = 0; c < 2 && ok; ++c)
+            ok = ts::make_pair_tensor_map(&g->tm_state[c], g->plane(2 * c), (int)nx, (int)ny,
+                                          L.pitch, L.plane_bytes, &why);
+        ok = ok && ts::make_pair_tensor_map(&g->tm_phase, g->pg(), (int)nx, (int)ny, L.pitch,
+                                            L.plane_bytes, &why);
         if (!ok) {
             if (g->owns_slab) cudaFree(g->slab);
             delete g;
@@ -337,12 +334,15 @@ ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
     g->dt = dt;
     g->theta = theta;
     g->J = dt != 0.0 ? 2.0 * theta / dt : 0.0;
-    // kinetic rotation in versine form, FP64, rounded once where used
-    const double sh1 = std::sin(0.5 * theta), sh2 = std::sin(theta);
+    // kinetic rotation coefficients in FP64, rounded once where used:
+    // versine form (g = 1 - cos theta = 2 sin^2(theta/2), s = sin theta) and
+    // lifting form (t = tan(theta/2), s); the merged angle 2 theta in lifting form
+    const double sh1 = std::sin(0.5 * theta);
     g->g1 = 2.0 * sh1 * sh1;
     g->s1 = std::sin(theta);
-    g->g2 = 2.0 * sh2 * sh2;
+    g->t1 = std::tan(0.5 * theta);
     g->s2 = std::sin(2.0 * theta);
+    g->t2 = std::tan(theta);
     const int nx = (int)g->L.nx, ny = (int)g->L.ny;
     cudaError_t e;
     if (!V) {
@@ -403,18 +403,17 @@ ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
     while (left > 0) {
         const int k = (int)(left >= K ? K : left);
         ts::FusedLaunch a;
-        a.tm_re = &g->tm_re[g->cur];
-        a.tm_im = &g->tm_im[g->cur];
-        a.tm_pg = &g->tm_pg;
-        a.tm_ps = &g->tm_ps;
+        a.tm_state = &g->tm_state[g->cur];
+        a.tm_phase = &g->tm_phase;
         a.out_re = (float *)g->re_other();
         a.out_im = (float *)g->im_other();
         a.nx = (int)g->L.nx;
         a.ny = (int)g->L.ny;
         a.pitch = g->L.pitch;
-        a.g1 = (float)g->g1;
+        a.t1 = (float)g->t1;
         a.s1 = (float)g->s1;
-        a.g2 = (float)g->g2;
+        a.g1 = (float)g->g1;
+        a.t2 = (float)g->t2;
         a.s2 = (float)g->s2;
         a.err = g->err;
         cudaError_t e = ts::launch_fused(k, a, st);
@@ -439,6 +438,11 @@ ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
             return fail(TS_ERR_UNSUPPORTED, "ts_evolve: FP64 grids run the plain path (K must be 0)");
         return plain_steps(g, steps, st);
     }
+    // The fused kernel applies the rotations at theta and 2 theta as three
+    // shears with tan(theta/2) and tan(theta); it requires |theta| <= pi/4
+    // (|2 theta| <= pi/2).  Larger angles -- far beyond any useful Trotter
+    // step -- run the one-sweep-per-kernel path.
+    if (std::fabs(g->theta) > 0.25 * M_PI) return plain_steps(g, steps, st);
     return fused_steps(g, steps, K == 0 ? auto_depth() : K, st);
 }
 

@@ -15,9 +15,10 @@
 //
 // Geometry ("warp streams").  A warp owns a strip of 128 columns (lane l
 // holds columns 4l..4l+3 of a row in registers as float4 re/im) and walks
-// down a range of rows.  Row pairs arrive through a ring of shared-memory
-// slots that TMA (cp.async.bulk.tensor.2d, 128 x 2 boxes of each of the four
-// planes) fills ahead of use; an mbarrier per slot tracks each fill.
+// down a range of rows.  Row pairs arrive through rings of shared-memory
+// slots that TMA fills ahead of use (cp.async.bulk.tensor.3d: one 128 x 2 x 2
+// box per slot covers the same two rows of two adjacent planes, (re, im) or
+// (gamma_V, s_V)); an mbarrier per slot tracks each fill.
 //  - X sweeps are row-local: pairs inside a lane's float4 rotate in
 //    registers, the pair that straddles two lanes uses warp shuffles.  The
 //    strip reads h = roundup(2K, 4) halo columns per side (the valid region
@@ -89,7 +90,7 @@ struct KParams {
     int n_strips, n_pairs;
     int64_t units;
     int total_warps;
-    float g1, s1, g2, s2;
+    float t1, s1, g1, t2, s2;
     int *err;
 };
 
@@ -146,30 +147,50 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     return true;
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y,
-                                            uint64_t *bar)
+// One box of two planes: x in [x, x+128), rows y, y+1, planes 0 and 1.
+__device__ __forceinline__ void tma_load_pair(void *dst, const CUtensorMap *tm, int x, int y,
+                                              uint64_t *bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(0), "r"(smem_addr(bar))
         : "memory");
 }
 
 // ---- register-level sweeps ------------------------------------------------
+// A pair rotation a' = c a + i s b, b' = i s a + c b splits into two real
+// plane rotations, of (a_re, b_im) and of (b_re, a_im), each by theta:
+//   x' = c x - s y, y' = s x + c y.
+// When a lane holds both members it applies each as three shears
+//   x -= t y;  y += s x;  x -= t y      (t = tan(theta/2), s = sin theta),
+// 6 FMA per pair instead of 8; every shear has determinant 1.  A lane that
+// holds one member of a pair (the pair straddling two lanes) updates only
+// that member, in the versine form a' = a - g a + i s b (4 FMA).
+__device__ __forceinline__ void rot_lift(float &ar, float &ai, float &br, float &bi, float t,
+                                         float s)
+{
+    ar = fmaf(-t, bi, ar);
+    br = fmaf(-t, ai, br);
+    bi = fmaf(s, ar, bi);
+    ai = fmaf(s, br, ai);
+    ar = fmaf(-t, bi, ar);
+    br = fmaf(-t, ai, br);
+}
+
 struct XEven {
-    float g0, s0, g1, s1;   // pairs (c0,c1) and (c2,c3) of the lane's float4
+    float t0, s0, t1, s1;   // pairs (c0,c1) and (c2,c3) of the lane's float4, lifting form
 };
 struct XOdd {
-    float g0, s0;           // pair (c1,c2), inside the lane
-    float gR, sR;           // pair (c3, next lane's c0)
-    float gL, sL;           // pair (previous lane's c3, c0)
+    float t0, s0;           // pair (c1,c2), inside the lane, lifting form
+    float gR, sR;           // pair (c3, next lane's c0), versine form
+    float gL, sL;           // pair (previous lane's c3, c0), versine form
 };
 
 __device__ __forceinline__ void x_even(Frag &f, const XEven &c)
 {
-    rot2(f.re.x, f.im.x, f.re.y, f.im.y, c.g0, c.s0);
-    rot2(f.re.z, f.im.z, f.re.w, f.im.w, c.g1, c.s1);
+    rot_lift(f.re.x, f.im.x, f.re.y, f.im.y, c.t0, c.s0);
+    rot_lift(f.re.z, f.im.z, f.re.w, f.im.w, c.t1, c.s1);
 }
 
 __device__ __forceinline__ void x_odd(Frag &f, const XOdd &c)
@@ -178,18 +199,18 @@ __device__ __forceinline__ void x_odd(Frag &f, const XOdd &c)
     const float ni = __shfl_down_sync(FULL, f.im.x, 1);
     const float pr = __shfl_up_sync(FULL, f.re.w, 1);
     const float pi = __shfl_up_sync(FULL, f.im.w, 1);
-    rot2(f.re.y, f.im.y, f.re.z, f.im.z, c.g0, c.s0);
+    rot_lift(f.re.y, f.im.y, f.re.z, f.im.z, c.t0, c.s0);
     rot1(f.re.w, f.im.w, nr, ni, c.gR, c.sR);
     rot1(f.re.x, f.im.x, pr, pi, c.gL, c.sL);
 }
 
-// Y pair rotation of two rows (all four columns of the lane).
-__device__ __forceinline__ void y_pair(Frag &a, Frag &b, float g, float s)
+// Y pair rotation of two rows (all four columns of the lane), lifting form.
+__device__ __forceinline__ void y_pair(Frag &a, Frag &b, float t, float s)
 {
-    rot2(a.re.x, a.im.x, b.re.x, b.im.x, g, s);
-    rot2(a.re.y, a.im.y, b.re.y, b.im.y, g, s);
-    rot2(a.re.z, a.im.z, b.re.z, b.im.z, g, s);
-    rot2(a.re.w, a.im.w, b.re.w, b.im.w, g, s);
+    rot_lift(a.re.x, a.im.x, b.re.x, b.im.x, t, s);
+    rot_lift(a.re.y, a.im.y, b.re.y, b.im.y, t, s);
+    rot_lift(a.re.z, a.im.z, b.re.z, b.im.z, t, s);
+    rot_lift(a.re.w, a.im.w, b.re.w, b.im.w, t, s);
 }
 
 __device__ __forceinline__ void phase4(Frag &f, float4 g, float4 s)
@@ -218,9 +239,8 @@ __device__ __forceinline__ float4 lds4(const unsigned char *slot, int plane, int
 
 template <int K>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32)
-fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ CUtensorMap tm_im,
-             const __grid_constant__ CUtensorMap tm_pg, const __grid_constant__ CUtensorMap tm_ps,
-             const KParams p)
+fused_kernel(const __grid_constant__ CUtensorMap tm_state,
+             const __grid_constant__ CUtensorMap tm_phase, const KParams p)
 {
     using C = Cfg<K>;
     constexpr int NSS = C::NSS, NSP = C::NSP, HALO = C::HALO, VALID = C::VALID;
@@ -267,9 +287,9 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
         auto xok = [&](int x) { return x >= 0 && x + 1 < p.nx; };
         const bool e0 = xok(xg), e1 = xok(xg + 2), o0 = xok(xg + 1), oR = xok(xg + 3),
                    oL = xok(xg - 1);
-        const XEven E1 = {e0 ? p.g1 : 0.f, e0 ? p.s1 : 0.f, e1 ? p.g1 : 0.f, e1 ? p.s1 : 0.f};
-        const XEven E2 = {e0 ? p.g2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.g2 : 0.f, e1 ? p.s2 : 0.f};
-        const XOdd O = {o0 ? p.g1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
+        const XEven E1 = {e0 ? p.t1 : 0.f, e0 ? p.s1 : 0.f, e1 ? p.t1 : 0.f, e1 ? p.s1 : 0.f};
+        const XEven E2 = {e0 ? p.t2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.t2 : 0.f, e1 ? p.s2 : 0.f};
+        const XOdd O = {o0 ? p.t1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
                         oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
         const bool store_lane =
             lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
@@ -280,16 +300,14 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
             unsigned char *slot = ring_s + (q % NSS) * SLOT_BYTES;
             uint64_t *bar = &bar_s[q % NSS];
             mbar_expect_tx(bar, SLOT_BYTES);
-            tma_load_2d(slot, &tm_re, XL, Ys + 2 * j, bar);
-            tma_load_2d(slot + PLANE_SLOT_BYTES, &tm_im, XL, Ys + 2 * j, bar);
+            tma_load_pair(slot, &tm_state, XL, Ys + 2 * j, bar);
         };
         auto issue_phase = [&](int j) {      // lane 0 only
             const uint32_t q = base + (uint32_t)j;
             unsigned char *slot = ring_p + (q % NSP) * SLOT_BYTES;
             uint64_t *bar = &bar_p[q % NSP];
             mbar_expect_tx(bar, SLOT_BYTES);
-            tma_load_2d(slot, &tm_pg, XL, Ys + 2 * j, bar);
-            tma_load_2d(slot + PLANE_SLOT_BYTES, &tm_ps, XL, Ys + 2 * j, bar);
+            tma_load_pair(slot, &tm_phase, XL, Ys + 2 * j, bar);
         };
         const int n_pro_s = n_iter < NSS ? n_iter : NSS;
         const int n_pro_p = n_iter < NSP ? n_iter : NSP;
@@ -349,11 +367,11 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
             x_odd(b, O);
             {
                 const bool v = yok(yin);
-                y_pair(a, b, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+                y_pair(a, b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
             }
             {
                 const bool v = yok(yin - 1);
-                y_pair(carry[0], a, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+                y_pair(carry[0], a, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
             }
             Frag P = carry[0], Q = a;     // rows (yin-1, yin)
             carry[0] = b;
@@ -370,7 +388,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
             for (int k = 1; k < K; ++k) {
                 {   // Yo (theta), aligned on (y1, y1+1), y1 odd
                     const bool v = yok(y1);
-                    y_pair(P, Q, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+                    y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
                 }
                 // X group between two phases: Xo, Xe(2 theta), Xo
                 x_odd(P, O);
@@ -381,13 +399,13 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
                 x_odd(Q, O);
                 {   // Ye (2 theta), shifted: pair (y1-1, y1)
                     const bool v = yok(y1 - 1);
-                    y_pair(carry[2 * k - 1], P, v ? p.g2 : 0.f, v ? p.s2 : 0.f);
+                    y_pair(carry[2 * k - 1], P, v ? p.t2 : 0.f, v ? p.s2 : 0.f);
                 }
                 Frag P2 = carry[2 * k - 1], Q2 = P;   // rows (y1-1, y1)
                 carry[2 * k - 1] = Q;
                 {   // Yo (theta), shifted: pair (y1-2, y1-1)
                     const bool v = yok(y1 - 2);
-                    y_pair(carry[2 * k], P2, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+                    y_pair(carry[2 * k], P2, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
                 }
                 P = carry[2 * k];                     // rows (y1-2, y1-1)
                 carry[2 * k] = Q2;
@@ -406,11 +424,11 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_re, const __grid_constant__ 
             // last step, second half: Yo aligned, Ye shifted, Xo, Xe
             {
                 const bool v = yok(y1);
-                y_pair(P, Q, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+                y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
             }
             {
                 const bool v = yok(y1 - 1);
-                y_pair(carry[2 * K - 1], P, v ? p.g1 : 0.f, v ? p.s1 : 0.f);
+                y_pair(carry[2 * K - 1], P, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
             }
             Frag O0 = carry[2 * K - 1], O1 = P;      // rows (y1-1, y1)
             carry[2 * K - 1] = Q;
@@ -481,14 +499,14 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     int64_t want = (p.units + 15) / 16;
     int64_t cap = (int64_t)num_sms * blocks_per_sm * WARPS_PER_CTA;
     p.total_warps = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-    p.g1 = a.g1;
+    p.t1 = a.t1;
     p.s1 = a.s1;
-    p.g2 = a.g2;
+    p.g1 = a.g1;
+    p.t2 = a.t2;
     p.s2 = a.s2;
     p.err = a.err;
     const int blocks = (p.total_warps + WARPS_PER_CTA - 1) / WARPS_PER_CTA;
-    fused_kernel<K><<<blocks, WARPS_PER_CTA * 32, C::SMEM, st>>>(*a.tm_re, *a.tm_im, *a.tm_pg,
-                                                                  *a.tm_ps, p);
+    fused_kernel<K><<<blocks, WARPS_PER_CTA * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -510,8 +528,8 @@ cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st)
     }
 }
 
-bool make_plane_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
-                           const char **why)
+bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
+                          size_t plane_bytes, const char **why)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -525,11 +543,11 @@ bool make_plane_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, in
         }
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
-    cuuint64_t strides[1] = {(cuuint64_t)(pitch * 4)};
-    cuuint32_t box[2] = {FUSED_BOX_COLS, FUSED_BOX_ROWS};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims,
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 2};
+    cuuint64_t strides[2] = {(cuuint64_t)(pitch * 4), (cuuint64_t)plane_bytes};
+    cuuint32_t box[3] = {FUSED_BOX_COLS, FUSED_BOX_ROWS, 2};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

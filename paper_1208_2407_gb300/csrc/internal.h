@@ -42,11 +42,14 @@ cudaError_t launch_observe(const void *re, const void *im, const void *vplane, b
 
 // --- fused temporally blocked path (fused.cu) -----------------------------
 struct FusedLaunch {
-    const CUtensorMap *tm_re, *tm_im, *tm_pg, *tm_ps;   // host copies, by value at launch
+    const CUtensorMap *tm_state;   // (re, im) planes of the input pair, 3-D map
+    const CUtensorMap *tm_phase;   // (gamma_V, s_V) planes, 3-D map
     float *out_re, *out_im;
     int nx, ny;
     int64_t pitch;
-    float g1, s1, g2, s2;    // rotation at theta and at 2 theta, versine form
+    // rotation at theta: lifting form (t1 = tan(theta/2), s1 = sin theta) and
+    // versine form (g1 = 1 - cos theta, s1); at 2 theta: lifting (t2, s2)
+    float t1, s1, g1, t2, s2;
     int *err;
 };
 constexpr int FUSED_MAX_K = 8;
@@ -54,11 +57,12 @@ constexpr int FUSED_BOX_COLS = 128;   // columns a warp strip loads (box width)
 constexpr int FUSED_BOX_ROWS = 2;     // rows per pipeline slot (box height)
 cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st);
 
-// Build a 2-D FP32 tensor map of an nx x ny pitched plane for the fused path.
-// Returns false (and a message) if the driver entry point is unavailable or
-// the encode call fails.
-bool make_plane_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
-                           const char **why);
+// Build a 3-D FP32 tensor map over two consecutive pitched planes (nx x ny
+// each, `plane_bytes` apart) for the fused path: one box load fetches the
+// same rows of both planes.  Returns false (and a message) if the driver
+// entry point is unavailable or the encode call fails.
+bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
+                          size_t plane_bytes, const char **why);
 
 // Thread-local count of kernel launches issued by this library.
 void count_launches(int64_t n);

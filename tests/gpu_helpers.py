@@ -41,3 +41,15 @@ def random_state(rng, nx, ny):
     im = rng.standard_normal((ny, nx))
     s = np.sqrt(np.sum(re * re + im * im))
     return re / s, im / s
+
+
+def grid_plane(g, index):
+    """A view of plane `index` of a grid's slab (0/1 state pair A, 2/3 pair B,
+    4 gamma_V, 5 s_V, 6 V) as an (ny, nx) tensor of the grid's dtype."""
+    import torch
+    L = g.layout
+    es = 8 if g.dtype == trotter.TS_F64 else 4
+    tdt = torch.float64 if es == 8 else torch.float32
+    start = index * int(L.plane_bytes)
+    raw = g.slab[start:start + int(L.pitch) * g.ny * es]
+    return raw.view(tdt).reshape(g.ny, int(L.pitch))[:, :g.nx]
