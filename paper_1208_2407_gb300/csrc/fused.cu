@@ -51,14 +51,25 @@ namespace ts {
 
 namespace {
 
-#ifndef TS_FUSED_WARPS_PER_CTA
-#define TS_FUSED_WARPS_PER_CTA 2
+#ifndef TS_FUSED_WPC_SHALLOW     // warps per CTA for K <= 2
+#define TS_FUSED_WPC_SHALLOW 2
 #endif
-#ifndef TS_FUSED_PREFETCH
-#define TS_FUSED_PREFETCH 2
+#ifndef TS_FUSED_WPC_DEEP        // ... and for K >= 3
+#define TS_FUSED_WPC_DEEP 1
 #endif
-constexpr int WARPS_PER_CTA = TS_FUSED_WARPS_PER_CTA;
-constexpr int PREFETCH = TS_FUSED_PREFETCH;          // D: row pairs in flight ahead of use
+#ifndef TS_FUSED_PF_SHALLOW      // row pairs prefetched ahead of use for K <= 2
+#define TS_FUSED_PF_SHALLOW 3
+#endif
+#ifndef TS_FUSED_PF_DEEP         // ... and for K >= 3
+#define TS_FUSED_PF_DEEP 1
+#endif
+#ifndef TS_FUSED_MIN_BLOCKS      // __launch_bounds__ minimum resident blocks per SM
+#define TS_FUSED_MIN_BLOCKS 1
+#endif
+#ifndef TS_FUSED_UNROLL          // unroll factor of the row-pair loop
+#define TS_FUSED_UNROLL 1
+#endif
+constexpr int ROW_LOOP_UNROLL = TS_FUSED_UNROLL;
 constexpr int PLANE_SLOT_BYTES = FUSED_BOX_ROWS * FUSED_BOX_COLS * 4;   // 1 KiB
 constexpr int SLOT_BYTES = 2 * PLANE_SLOT_BYTES;     // one ring slot: two planes of 2 rows
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;    // 2 s per wait
@@ -66,17 +77,21 @@ constexpr uint32_t FULL = 0xffffffffu;
 
 // Two rings per warp, both indexed by the row pair j (rows Ys + 2j, +1):
 //  - the state ring (re, im) is read once, when row pair j enters the
-//    pipeline, so it needs PREFETCH + 1 slots;
+//    pipeline, so it needs PF + 1 slots;
 //  - the phase ring (gamma_V, s_V) is read by the phase of every step, the
-//    last one K row pairs later, so it needs PREFETCH + K + 1 slots.
+//    last one K row pairs later, so it needs PF + K + 1 slots.
+// Shallow pipelines are memory bound and prefetch deeper; deep ones are
+// arithmetic bound and keep shared memory small for occupancy.
 template <int K>
 struct Cfg {
-    static constexpr int NSS = PREFETCH + 1;
-    static constexpr int NSP = PREFETCH + K + 1;
+    static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
+    static constexpr int PF = K <= 2 ? TS_FUSED_PF_SHALLOW : TS_FUSED_PF_DEEP;
+    static constexpr int NSS = PF + 1;
+    static constexpr int NSP = PF + K + 1;
     static constexpr int HALO = ((2 * K + 3) / 4) * 4;
     static constexpr int VALID = FUSED_BOX_COLS - 2 * HALO;
     static constexpr int WARP_SMEM = (NSS + NSP) * SLOT_BYTES;
-    static constexpr int SMEM = 1024 + WARPS_PER_CTA * (WARP_SMEM + (NSS + NSP) * 8);
+    static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + (NSS + NSP) * 8);
 };
 
 struct Frag {
@@ -237,13 +252,117 @@ __device__ __forceinline__ float4 lds4(const unsigned char *slot, int plane, int
                                              row * (FUSED_BOX_COLS * 4) + lane * 16);
 }
 
+// Per-lane coefficients of one strip (x masks applied) and the scalars.
+struct StripCoef {
+    XEven E1, E2;   // even pairs at theta and 2 theta
+    XOdd O;         // odd pairs at theta
+};
+
+// One row pair through the K-step pipeline.  INTERIOR: every Y pair and
+// every phase row the iteration touches lies on the grid and in the ring,
+// so no masks or range checks are needed.
+template <int K, bool INTERIOR>
+__device__ __forceinline__ void pipeline_step(Frag (&carry)[2 * K], Frag a, Frag b, int yin, int j,
+                                              const unsigned char *ring_p, int pos_p,
+                                              const StripCoef &c, const KParams &p, int lane,
+                                              Frag &O0, Frag &O1)
+{
+    using C = Cfg<K>;
+    constexpr int NSP = C::NSP;
+    auto yok = [&](int y) { return INTERIOR || (y >= 0 && y + 1 < p.ny); };
+    auto slot_p = [&](int back) -> const unsigned char * {   // phase slot j - back
+        int q = pos_p - back;
+        if (q < 0) q += NSP;
+        return ring_p + q * SLOT_BYTES;
+    };
+    // step 0, first half: Xe, Xo (row-local), Ye aligned, Yo shifted
+    x_even(a, c.E1);
+    x_even(b, c.E1);
+    x_odd(a, c.O);
+    x_odd(b, c.O);
+    {
+        const bool v = yok(yin);
+        y_pair(a, b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+    }
+    {
+        const bool v = yok(yin - 1);
+        y_pair(carry[0], a, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+    }
+    Frag P = carry[0], Q = a;     // rows (yin-1, yin)
+    carry[0] = b;
+    int y1 = yin - 1;
+    // phase of step 0 on rows (y1, y1+1): slot j-1 row 1, slot j row 0
+    if (INTERIOR || j >= 1) {
+        const unsigned char *sp = slot_p(1);
+        phase4(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
+    }
+    {
+        const unsigned char *sp = slot_p(0);
+        phase4(Q, lds4(sp, 0, 0, lane), lds4(sp, 1, 0, lane));
+    }
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+        {   // Yo (theta), aligned on (y1, y1+1), y1 odd
+            const bool v = yok(y1);
+            y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+        }
+        // X group between two phases: Xo, Xe(2 theta), Xo
+        x_odd(P, c.O);
+        x_odd(Q, c.O);
+        x_even(P, c.E2);
+        x_even(Q, c.E2);
+        x_odd(P, c.O);
+        x_odd(Q, c.O);
+        {   // Ye (2 theta), shifted: pair (y1-1, y1)
+            const bool v = yok(y1 - 1);
+            y_pair(carry[2 * k - 1], P, v ? p.t2 : 0.f, v ? p.s2 : 0.f);
+        }
+        Frag P2 = carry[2 * k - 1], Q2 = P;   // rows (y1-1, y1)
+        carry[2 * k - 1] = Q;
+        {   // Yo (theta), shifted: pair (y1-2, y1-1)
+            const bool v = yok(y1 - 2);
+            y_pair(carry[2 * k], P2, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+        }
+        P = carry[2 * k];                     // rows (y1-2, y1-1)
+        carry[2 * k] = Q2;
+        Q = P2;
+        y1 -= 2;
+        // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
+        if (INTERIOR || j - k - 1 >= 0) {
+            const unsigned char *sp = slot_p(k + 1);
+            phase4(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
+        }
+        if (INTERIOR || j - k >= 0) {
+            const unsigned char *sp = slot_p(k);
+            phase4(Q, lds4(sp, 0, 0, lane), lds4(sp, 1, 0, lane));
+        }
+    }
+    // last step, second half: Yo aligned, Ye shifted, Xo, Xe
+    {
+        const bool v = yok(y1);
+        y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+    }
+    {
+        const bool v = yok(y1 - 1);
+        y_pair(carry[2 * K - 1], P, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+    }
+    O0 = carry[2 * K - 1];    // rows (y1-1, y1) = (yin-2K, yin-2K+1)
+    O1 = P;
+    carry[2 * K - 1] = Q;
+    x_odd(O0, c.O);
+    x_odd(O1, c.O);
+    x_even(O0, c.E1);
+    x_even(O1, c.E1);
+}
+
 template <int K>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32)
+__global__ void __launch_bounds__(Cfg<K>::WPC * 32, TS_FUSED_MIN_BLOCKS)
 fused_kernel(const __grid_constant__ CUtensorMap tm_state,
              const __grid_constant__ CUtensorMap tm_phase, const KParams p)
 {
     using C = Cfg<K>;
     constexpr int NSS = C::NSS, NSP = C::NSP, HALO = C::HALO, VALID = C::VALID;
+    constexpr int WARPS_PER_CTA = C::WPC;
 
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -267,7 +386,10 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
 
     const int64_t u_begin = (int64_t)gw * p.units / p.total_warps;
     const int64_t u_end = (int64_t)(gw + 1) * p.units / p.total_warps;
-    uint32_t seq = 0;       // row pairs issued (and consumed) by this warp so far
+    // ring positions and mbarrier phase parities of the next row pair to be
+    // consumed; they carry over from one row range to the next
+    int pos_s = 0, pos_p = 0;
+    uint32_t par_s = 0, par_p = 0;
     bool failed = false;
 
     for (int64_t u = u_begin; u < u_end && !failed;) {
@@ -287,157 +409,72 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
         auto xok = [&](int x) { return x >= 0 && x + 1 < p.nx; };
         const bool e0 = xok(xg), e1 = xok(xg + 2), o0 = xok(xg + 1), oR = xok(xg + 3),
                    oL = xok(xg - 1);
-        const XEven E1 = {e0 ? p.t1 : 0.f, e0 ? p.s1 : 0.f, e1 ? p.t1 : 0.f, e1 ? p.s1 : 0.f};
-        const XEven E2 = {e0 ? p.t2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.t2 : 0.f, e1 ? p.s2 : 0.f};
-        const XOdd O = {o0 ? p.t1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
-                        oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
+        StripCoef c;
+        c.E1 = {e0 ? p.t1 : 0.f, e0 ? p.s1 : 0.f, e1 ? p.t1 : 0.f, e1 ? p.s1 : 0.f};
+        c.E2 = {e0 ? p.t2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.t2 : 0.f, e1 ? p.s2 : 0.f};
+        c.O = {o0 ? p.t1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
+               oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
         const bool store_lane =
             lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
 
-        const uint32_t base = seq;
-        auto issue_state = [&](int j) {      // lane 0 only
-            const uint32_t q = base + (uint32_t)j;
-            unsigned char *slot = ring_s + (q % NSS) * SLOT_BYTES;
-            uint64_t *bar = &bar_s[q % NSS];
-            mbar_expect_tx(bar, SLOT_BYTES);
-            tma_load_pair(slot, &tm_state, XL, Ys + 2 * j, bar);
+        // lane 0 only: fill ring position `pos` with row pair j
+        auto issue_state = [&](int pos, int j) {
+            mbar_expect_tx(&bar_s[pos], SLOT_BYTES);
+            tma_load_pair(ring_s + pos * SLOT_BYTES, &tm_state, XL, Ys + 2 * j, &bar_s[pos]);
         };
-        auto issue_phase = [&](int j) {      // lane 0 only
-            const uint32_t q = base + (uint32_t)j;
-            unsigned char *slot = ring_p + (q % NSP) * SLOT_BYTES;
-            uint64_t *bar = &bar_p[q % NSP];
-            mbar_expect_tx(bar, SLOT_BYTES);
-            tma_load_pair(slot, &tm_phase, XL, Ys + 2 * j, bar);
+        auto issue_phase = [&](int pos, int j) {
+            mbar_expect_tx(&bar_p[pos], SLOT_BYTES);
+            tma_load_pair(ring_p + pos * SLOT_BYTES, &tm_phase, XL, Ys + 2 * j, &bar_p[pos]);
         };
         const int n_pro_s = n_iter < NSS ? n_iter : NSS;
         const int n_pro_p = n_iter < NSP ? n_iter : NSP;
         if (lane == 0) {
             fence_proxy_async();
             for (int j = 0; j < n_pro_p; ++j) {
-                if (j < n_pro_s) issue_state(j);
-                issue_phase(j);
+                if (j < n_pro_s) issue_state((pos_s + j) % NSS, j);
+                issue_phase((pos_p + j) % NSP, j);
             }
         }
         int issued_s = n_pro_s, issued_p = n_pro_p;
-
-        auto state_slot = [&](int j) -> const unsigned char * {
-            return ring_s + ((base + (uint32_t)j) % NSS) * SLOT_BYTES;
-        };
-        auto phase_slot = [&](int j) -> const unsigned char * {
-            return ring_p + ((base + (uint32_t)j) % NSP) * SLOT_BYTES;
-        };
-        auto yok = [&](int y) { return y >= 0 && y + 1 < p.ny; };
 
         Frag carry[2 * K];
 #pragma unroll
         for (int i = 0; i < 2 * K; ++i) carry[i] = zero_frag();
 
+#pragma unroll ROW_LOOP_UNROLL
         for (int j = 0; j < n_iter; ++j) {
-            const uint32_t q = base + (uint32_t)j;
-            bool ok = mbar_wait(&bar_s[q % NSS], (q / NSS) & 1u, WAIT_LIMIT_NS) &&
-                      mbar_wait(&bar_p[q % NSP], (q / NSP) & 1u, WAIT_LIMIT_NS);
+            bool ok = mbar_wait(&bar_s[pos_s], par_s, WAIT_LIMIT_NS) &&
+                      mbar_wait(&bar_p[pos_p], par_p, WAIT_LIMIT_NS);
             ok = __all_sync(FULL, ok);
             if (!ok) {
                 failed = true;
                 if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
                 // drain this warp's outstanding copies (bounded) before leaving
-                for (int jj = j; jj < issued_s; ++jj) {
-                    const uint32_t qq = base + (uint32_t)jj;
-                    mbar_wait(&bar_s[qq % NSS], (qq / NSS) & 1u, WAIT_LIMIT_NS / 4);
+                for (int jj = j, ps = pos_s, ph = par_s; jj < issued_s; ++jj) {
+                    mbar_wait(&bar_s[ps], ph, WAIT_LIMIT_NS / 4);
+                    if (++ps == NSS) { ps = 0; ph ^= 1u; }
                 }
-                for (int jj = j; jj < issued_p; ++jj) {
-                    const uint32_t qq = base + (uint32_t)jj;
-                    mbar_wait(&bar_p[qq % NSP], (qq / NSP) & 1u, WAIT_LIMIT_NS / 4);
+                for (int jj = j, ps = pos_p, ph = par_p; jj < issued_p; ++jj) {
+                    mbar_wait(&bar_p[ps], ph, WAIT_LIMIT_NS / 4);
+                    if (++ps == NSP) { ps = 0; ph ^= 1u; }
                 }
                 break;
             }
-            const unsigned char *sj = state_slot(j);
-            const unsigned char *pj = phase_slot(j);
+            const unsigned char *sj = ring_s + pos_s * SLOT_BYTES;
             Frag a, b;
             a.re = lds4(sj, 0, 0, lane);
             a.im = lds4(sj, 1, 0, lane);
             b.re = lds4(sj, 0, 1, lane);
             b.im = lds4(sj, 1, 1, lane);
             const int yin = Ys + 2 * j;
+            Frag O0, O1;
+            const bool interior = j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny;
+            if (interior)
+                pipeline_step<K, true>(carry, a, b, yin, j, ring_p, pos_p, c, p, lane, O0, O1);
+            else
+                pipeline_step<K, false>(carry, a, b, yin, j, ring_p, pos_p, c, p, lane, O0, O1);
 
-            // step 0, first half: Xe, Xo (row-local), Ye aligned, Yo shifted
-            x_even(a, E1);
-            x_even(b, E1);
-            x_odd(a, O);
-            x_odd(b, O);
-            {
-                const bool v = yok(yin);
-                y_pair(a, b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
-            }
-            {
-                const bool v = yok(yin - 1);
-                y_pair(carry[0], a, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
-            }
-            Frag P = carry[0], Q = a;     // rows (yin-1, yin)
-            carry[0] = b;
-            int y1 = yin - 1;
-            // phase of step 0 on rows (y1, y1+1): slot j-1 row 1, slot j row 0
-            {
-                if (j >= 1) {
-                    const unsigned char *sp = phase_slot(j - 1);
-                    phase4(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
-                }
-                phase4(Q, lds4(pj, 0, 0, lane), lds4(pj, 1, 0, lane));
-            }
-#pragma unroll
-            for (int k = 1; k < K; ++k) {
-                {   // Yo (theta), aligned on (y1, y1+1), y1 odd
-                    const bool v = yok(y1);
-                    y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
-                }
-                // X group between two phases: Xo, Xe(2 theta), Xo
-                x_odd(P, O);
-                x_odd(Q, O);
-                x_even(P, E2);
-                x_even(Q, E2);
-                x_odd(P, O);
-                x_odd(Q, O);
-                {   // Ye (2 theta), shifted: pair (y1-1, y1)
-                    const bool v = yok(y1 - 1);
-                    y_pair(carry[2 * k - 1], P, v ? p.t2 : 0.f, v ? p.s2 : 0.f);
-                }
-                Frag P2 = carry[2 * k - 1], Q2 = P;   // rows (y1-1, y1)
-                carry[2 * k - 1] = Q;
-                {   // Yo (theta), shifted: pair (y1-2, y1-1)
-                    const bool v = yok(y1 - 2);
-                    y_pair(carry[2 * k], P2, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
-                }
-                P = carry[2 * k];                     // rows (y1-2, y1-1)
-                carry[2 * k] = Q2;
-                Q = P2;
-                y1 -= 2;
-                // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
-                if (j - k - 1 >= 0) {
-                    const unsigned char *sp = phase_slot(j - k - 1);
-                    phase4(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
-                }
-                if (j - k >= 0) {
-                    const unsigned char *sq = phase_slot(j - k);
-                    phase4(Q, lds4(sq, 0, 0, lane), lds4(sq, 1, 0, lane));
-                }
-            }
-            // last step, second half: Yo aligned, Ye shifted, Xo, Xe
-            {
-                const bool v = yok(y1);
-                y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
-            }
-            {
-                const bool v = yok(y1 - 1);
-                y_pair(carry[2 * K - 1], P, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
-            }
-            Frag O0 = carry[2 * K - 1], O1 = P;      // rows (y1-1, y1)
-            carry[2 * K - 1] = Q;
-            x_odd(O0, O);
-            x_odd(O1, O);
-            x_even(O0, E1);
-            x_even(O1, E1);
-
-            const int yo = y1 - 1;                    // == yin - 2K
+            const int yo = yin - 2 * K;
             if (store_lane && yo >= Y0 && yo < Y1) {
                 float *r = p.out_re + (int64_t)yo * p.pitch + xg;
                 float *m = p.out_im + (int64_t)yo * p.pitch + xg;
@@ -452,18 +489,20 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
             }
 
             // state slot j and phase slot j-K are no longer read: refill them
+            // with row pairs j + NSS and j - K + NSP (the same ring positions)
             __syncwarp();
             const int js = j + NSS, jp = j - K + NSP;
             const bool more_s = js < n_iter, more_p = j >= K && jp < n_iter;
             if (lane == 0 && (more_s || more_p)) {
                 fence_proxy_async();
-                if (more_s) issue_state(js);
-                if (more_p) issue_phase(jp);
+                if (more_s) issue_state(pos_s, js);
+                if (more_p) issue_phase(pos_p - K < 0 ? pos_p - K + NSP : pos_p - K, jp);
             }
             issued_s += more_s;
             issued_p += more_p;
+            if (++pos_s == NSS) { pos_s = 0; par_s ^= 1u; }
+            if (++pos_p == NSP) { pos_p = 0; par_p ^= 1u; }
         }
-        seq = base + (uint32_t)n_iter;
         __syncwarp();
     }
 }
@@ -482,7 +521,7 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fused_kernel<K>,
-                                                          WARPS_PER_CTA * 32, C::SMEM);
+                                                          C::WPC * 32, C::SMEM);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
     }
@@ -497,7 +536,7 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.units = (int64_t)p.n_strips * p.n_pairs;
     // at least ~16 row pairs per warp, at most the resident warps
     int64_t want = (p.units + 15) / 16;
-    int64_t cap = (int64_t)num_sms * blocks_per_sm * WARPS_PER_CTA;
+    int64_t cap = (int64_t)num_sms * blocks_per_sm * C::WPC;
     p.total_warps = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     p.t1 = a.t1;
     p.s1 = a.s1;
@@ -505,8 +544,8 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.t2 = a.t2;
     p.s2 = a.s2;
     p.err = a.err;
-    const int blocks = (p.total_warps + WARPS_PER_CTA - 1) / WARPS_PER_CTA;
-    fused_kernel<K><<<blocks, WARPS_PER_CTA * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
+    const int blocks = (p.total_warps + C::WPC - 1) / C::WPC;
+    fused_kernel<K><<<blocks, C::WPC * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -549,7 +588,7 @@ bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         *why = "cuTensorMapEncodeTiled rejected the plane layout";
