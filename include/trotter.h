@@ -148,6 +148,38 @@ ts_status ts_energy(ts_grid *g, double *out, void *stream);   /* e_kin + e_pot *
 ts_status ts_evolve_batched(ts_grid *const *g, int n, const int64_t *steps, int K,
                             void *stream);
 
+/* Adjoint: gradient of the fidelity F = |<phi|psi_T>|^2 with respect to the
+ * potential V on every site, where psi_T = U2(dt)^steps psi_0 evolves the
+ * grid's current state with its current potential, dt and theta.
+ * Write a step as psi_s = B P A psi_{s-1} (A, B: the first and last four
+ * sweeps, P = exp(-i V dt)); with c = <phi|psi_T>, lambda_T = phi,
+ * lambda_{s-1} = U_s^dagger lambda_s and m_s = P A psi_{s-1}:
+ *   dF/dV_j = 2 dt Im( conj(c) sum_s conj((B^dagger lambda_s)[j]) m_s[j] ).
+ * U^dagger is the step at -theta with the conjugate phase; the backward pass
+ * runs it as a hand-written kernel and recomputes the m_s of each segment of
+ * `ckpt_every` steps from a checkpoint of psi.  FP32 grids, |theta| <= pi/4.
+ *
+ * ts_adjoint_workspace: bytes of device workspace for (steps, ckpt_every):
+ *   about (14 + 2 ceil(steps/ckpt) + 2 ckpt) planes of the grid.
+ * ts_adjoint_forward: target phi as dense arrays (host or device, FP32 or
+ *   FP64); evolves the grid's state by `steps` (the grid then holds psi_T),
+ *   keeps checkpoints in `ws` (caller-owned, 256-byte aligned), returns F
+ *   (and c = overlap[0] + i overlap[1] if overlap != NULL).  Syncs.
+ * ts_adjoint_backward: after a forward with the same ws, writes dF/dV as a
+ *   dense nx*ny FP32 device array `grad`.  Syncs.  One forward/backward pair
+ *   per grid at a time; TS_ERR_STATE without a matching forward.
+ * ts_adjoint_grad: forward then backward. */
+ts_status ts_adjoint_workspace(const ts_grid *g, int64_t steps, int64_t ckpt_every,
+                               size_t *bytes);
+ts_status ts_adjoint_forward(ts_grid *g, const void *target_re, const void *target_im,
+                             ts_dtype target_dtype, ts_mem where, int64_t steps,
+                             int64_t ckpt_every, void *ws, size_t ws_bytes, double *fidelity,
+                             double *overlap, void *stream);
+ts_status ts_adjoint_backward(ts_grid *g, void *ws, size_t ws_bytes, float *grad, void *stream);
+ts_status ts_adjoint_grad(ts_grid *g, const void *target_re, const void *target_im,
+                          ts_dtype target_dtype, ts_mem where, int64_t steps, int64_t ckpt_every,
+                          void *ws, size_t ws_bytes, float *grad, double *fidelity, void *stream);
+
 /* Sum of |psi|^2 over a pitched device state, without allocating anything.
  *
  * The paper has no counterpart: this entry point exists for callers that

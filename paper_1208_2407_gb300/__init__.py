@@ -10,7 +10,7 @@ __all__ = ["trotter", "workloads"]
 
 
 def __getattr__(name):
-    if name in ("trotter", "workloads", "build"):
+    if name in ("trotter", "workloads", "build", "autograd"):
         import importlib
         return importlib.import_module("." + name, __name__)
     raise AttributeError(name)

@@ -11,6 +11,7 @@
 #include <new>
 
 #include "../../include/trotter.h"
+#include "grid.h"
 #include "internal.h"
 
 namespace {
@@ -45,30 +46,6 @@ size_t scratch_bytes()
 }
 
 }  // namespace
-
-struct ts_grid {
-    ts_layout L;
-    size_t esize;
-    unsigned char *slab;
-    bool owns_slab;
-    int cur;                 // 0: planes 0/1 hold the state, 1: planes 2/3
-    double dt, theta, J;
-    double g1, s1, t1, s2, t2;   // rotation coefficients (FP64): theta and 2 theta
-    double *partials, *result;
-    int *err;
-    bool tmaps_ok;
-    CUtensorMap tm_state[2], tm_phase;   // (re, im) of pair 0 / 1; (gamma_V, s_V)
-
-    void *plane(int i) const { return slab + (size_t)i * L.plane_bytes; }
-    void *re() const { return plane(2 * cur); }
-    void *im() const { return plane(2 * cur + 1); }
-    void *re_other() const { return plane(2 * (cur ^ 1)); }
-    void *im_other() const { return plane(2 * (cur ^ 1) + 1); }
-    void *pg() const { return plane(4); }
-    void *ps() const { return plane(5); }
-    void *vp() const { return plane(6); }
-    bool f64() const { return L.dtype == TS_F64; }
-};
 
 namespace ts {
 void count_launches(int64_t n) { g_launches += n; }
@@ -181,6 +158,7 @@ ts_status ts_create_grid(int64_t nx, int64_t ny, ts_dtype dtype, void *slab, siz
 ts_status ts_destroy_grid(ts_grid *g)
 {
     if (!g) return TS_OK;
+    ts::forget_adjoint(g);
     cudaError_t e = cudaSuccess;
     if (g->owns_slab) e = cudaFree(g->slab);
     delete g;

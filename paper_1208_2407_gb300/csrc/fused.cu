@@ -45,6 +45,7 @@
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
+#include "ffloat.cuh"
 #include "internal.h"
 
 namespace ts {
@@ -107,6 +108,12 @@ struct KParams {
     int total_warps;
     float t1, s1, g1, t2, s2;
     int *err;
+    // adjoint support (K = 1 only): MODE 1 writes the mid-step state m (after
+    // the phase) to (m_re, m_im); MODE 2 reads it and accumulates
+    // G += conj(lt) m, with lt the state at the phase point, into the
+    // double-float planes (g_rh + g_rl, g_ih + g_il)
+    float *m_re, *m_im;
+    float *g_rh, *g_rl, *g_ih, *g_il;
 };
 
 // ---- PTX wrappers ---------------------------------------------------------
@@ -258,15 +265,76 @@ struct StripCoef {
     XOdd O;         // odd pairs at theta
 };
 
+// Rows and columns this warp owns in its current row range.
+struct Owned {
+    int Y0, Y1;        // output rows [Y0, Y1)
+    int xg;            // the lane's first column
+    bool lane_ok;      // the lane's 4 columns are inside the valid strip and < nx
+};
+
+__device__ __forceinline__ bool owns_row(const Owned &w, const KParams &p, int row)
+{
+    return w.lane_ok && row >= w.Y0 && row < w.Y1 && row < p.ny;
+}
+
+// Adjoint hook at the phase point of a backward step: G += conj(lt) m for one
+// owned row (lt = this row of the costate after B^dagger, m = the forward
+// mid-step state of the same step).
+__device__ __forceinline__ void mid_accumulate(const Frag &lt, int row, const Owned &w,
+                                               const KParams &p)
+{
+    const int64_t o = (int64_t)row * p.pitch + w.xg;
+    const float4 mr = *reinterpret_cast<const float4 *>(p.m_re + o);
+    const float4 mi = *reinterpret_cast<const float4 *>(p.m_im + o);
+    float4 rh = *reinterpret_cast<const float4 *>(p.g_rh + o);
+    float4 rl = *reinterpret_cast<const float4 *>(p.g_rl + o);
+    float4 ih = *reinterpret_cast<const float4 *>(p.g_ih + o);
+    float4 il = *reinterpret_cast<const float4 *>(p.g_il + o);
+    auto acc = [](float &hi, float &lo, float v) {
+        FF s = two_sum(hi, v);
+        s.lo += lo;
+        s = fast_two_sum(s.hi, s.lo);
+        hi = s.hi;
+        lo = s.lo;
+    };
+    // conj(l) m = (lr mr + li mi) + i (lr mi - li mr)
+    acc(rh.x, rl.x, fmaf(lt.re.x, mr.x, lt.im.x * mi.x));
+    acc(rh.y, rl.y, fmaf(lt.re.y, mr.y, lt.im.y * mi.y));
+    acc(rh.z, rl.z, fmaf(lt.re.z, mr.z, lt.im.z * mi.z));
+    acc(rh.w, rl.w, fmaf(lt.re.w, mr.w, lt.im.w * mi.w));
+    acc(ih.x, il.x, fmaf(lt.re.x, mi.x, -lt.im.x * mr.x));
+    acc(ih.y, il.y, fmaf(lt.re.y, mi.y, -lt.im.y * mr.y));
+    acc(ih.z, il.z, fmaf(lt.re.z, mi.z, -lt.im.z * mr.z));
+    acc(ih.w, il.w, fmaf(lt.re.w, mi.w, -lt.im.w * mr.w));
+    *reinterpret_cast<float4 *>(p.g_rh + o) = rh;
+    *reinterpret_cast<float4 *>(p.g_rl + o) = rl;
+    *reinterpret_cast<float4 *>(p.g_ih + o) = ih;
+    *reinterpret_cast<float4 *>(p.g_il + o) = il;
+}
+
+__device__ __forceinline__ void mid_store(const Frag &m, int row, const Owned &w,
+                                          const KParams &p)
+{
+    const int64_t o = (int64_t)row * p.pitch + w.xg;
+    *reinterpret_cast<float4 *>(p.m_re + o) = m.re;
+    *reinterpret_cast<float4 *>(p.m_im + o) = m.im;
+}
+
+__device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+
 // One row pair through the K-step pipeline.  INTERIOR: every Y pair and
 // every phase row the iteration touches lies on the grid and in the ring,
-// so no masks or range checks are needed.
-template <int K, bool INTERIOR>
+// so no masks or range checks are needed.  MODE 0: a plain step; MODE 1
+// (K = 1): also store the mid-step state; MODE 2 (K = 1): a backward step
+// U^dagger (the caller passes the coefficients at -theta; the phase is
+// conjugated here) that accumulates G at its phase point.
+template <int K, bool INTERIOR, int MODE>
 __device__ __forceinline__ void pipeline_step(Frag (&carry)[2 * K], Frag a, Frag b, int yin, int j,
                                               const unsigned char *ring_p, int pos_p,
                                               const StripCoef &c, const KParams &p, int lane,
-                                              Frag &O0, Frag &O1)
+                                              const Owned &w, Frag &O0, Frag &O1)
 {
+    static_assert(MODE == 0 || K == 1, "mid-step modes exist for K = 1 only");
     using C = Cfg<K>;
     constexpr int NSP = C::NSP;
     auto yok = [&](int y) { return INTERIOR || (y >= 0 && y + 1 < p.ny); };
@@ -291,14 +359,25 @@ __device__ __forceinline__ void pipeline_step(Frag (&carry)[2 * K], Frag a, Frag
     Frag P = carry[0], Q = a;     // rows (yin-1, yin)
     carry[0] = b;
     int y1 = yin - 1;
+    if constexpr (MODE == 2) {
+        if (owns_row(w, p, y1)) mid_accumulate(P, y1, w, p);
+        if (owns_row(w, p, y1 + 1)) mid_accumulate(Q, y1 + 1, w, p);
+    }
     // phase of step 0 on rows (y1, y1+1): slot j-1 row 1, slot j row 0
+    // (conjugated in a backward step: exp(+i V dt) has sine -s_V)
     if (INTERIOR || j >= 1) {
         const unsigned char *sp = slot_p(1);
-        phase4(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
+        const float4 sv = lds4(sp, 1, 1, lane);
+        phase4(P, lds4(sp, 0, 1, lane), MODE == 2 ? neg4(sv) : sv);
     }
     {
         const unsigned char *sp = slot_p(0);
-        phase4(Q, lds4(sp, 0, 0, lane), lds4(sp, 1, 0, lane));
+        const float4 sv = lds4(sp, 1, 0, lane);
+        phase4(Q, lds4(sp, 0, 0, lane), MODE == 2 ? neg4(sv) : sv);
+    }
+    if constexpr (MODE == 1) {
+        if (owns_row(w, p, y1)) mid_store(P, y1, w, p);
+        if (owns_row(w, p, y1 + 1)) mid_store(Q, y1 + 1, w, p);
     }
 #pragma unroll
     for (int k = 1; k < K; ++k) {
@@ -355,7 +434,7 @@ __device__ __forceinline__ void pipeline_step(Frag (&carry)[2 * K], Frag a, Frag
     x_even(O1, c.E1);
 }
 
-template <int K>
+template <int K, int MODE>
 __global__ void __launch_bounds__(Cfg<K>::WPC * 32, TS_FUSED_MIN_BLOCKS)
 fused_kernel(const __grid_constant__ CUtensorMap tm_state,
              const __grid_constant__ CUtensorMap tm_phase, const KParams p)
@@ -416,6 +495,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
                oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
         const bool store_lane =
             lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
+        const Owned own = {Y0, Y1, xg, store_lane};
 
         // lane 0 only: fill ring position `pos` with row pair j
         auto issue_state = [&](int pos, int j) {
@@ -470,9 +550,11 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
             Frag O0, O1;
             const bool interior = j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny;
             if (interior)
-                pipeline_step<K, true>(carry, a, b, yin, j, ring_p, pos_p, c, p, lane, O0, O1);
+                pipeline_step<K, true, MODE>(carry, a, b, yin, j, ring_p, pos_p, c, p, lane, own,
+                                             O0, O1);
             else
-                pipeline_step<K, false>(carry, a, b, yin, j, ring_p, pos_p, c, p, lane, O0, O1);
+                pipeline_step<K, false, MODE>(carry, a, b, yin, j, ring_p, pos_p, c, p, lane, own,
+                                              O0, O1);
 
             const int yo = yin - 2 * K;
             if (store_lane && yo >= Y0 && yo < Y1) {
@@ -507,20 +589,20 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
     }
 }
 
-template <int K>
+template <int K, int MODE>
 cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
 {
     using C = Cfg<K>;
     static int blocks_per_sm = -1;
     static int num_sms = 0;
     if (blocks_per_sm < 0) {
-        cudaError_t e = cudaFuncSetAttribute(fused_kernel<K>,
+        cudaError_t e = cudaFuncSetAttribute(fused_kernel<K, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fused_kernel<K>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fused_kernel<K, MODE>,
                                                           C::WPC * 32, C::SMEM);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -544,8 +626,14 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.t2 = a.t2;
     p.s2 = a.s2;
     p.err = a.err;
+    p.m_re = a.m_re;
+    p.m_im = a.m_im;
+    p.g_rh = a.g_rh;
+    p.g_rl = a.g_rl;
+    p.g_ih = a.g_ih;
+    p.g_il = a.g_il;
     const int blocks = (p.total_warps + C::WPC - 1) / C::WPC;
-    fused_kernel<K><<<blocks, C::WPC * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
+    fused_kernel<K, MODE><<<blocks, C::WPC * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -555,16 +643,23 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
 cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st)
 {
     switch (K) {
-    case 1: return launch_k<1>(a, st);
-    case 2: return launch_k<2>(a, st);
-    case 3: return launch_k<3>(a, st);
-    case 4: return launch_k<4>(a, st);
-    case 5: return launch_k<5>(a, st);
-    case 6: return launch_k<6>(a, st);
-    case 7: return launch_k<7>(a, st);
-    case 8: return launch_k<8>(a, st);
+    case 1: return launch_k<1, 0>(a, st);
+    case 2: return launch_k<2, 0>(a, st);
+    case 3: return launch_k<3, 0>(a, st);
+    case 4: return launch_k<4, 0>(a, st);
+    case 5: return launch_k<5, 0>(a, st);
+    case 6: return launch_k<6, 0>(a, st);
+    case 7: return launch_k<7, 0>(a, st);
+    case 8: return launch_k<8, 0>(a, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st)
+{
+    if (mode == 1) return launch_k<1, 1>(a, st);
+    if (mode == 2) return launch_k<1, 2>(a, st);
+    return cudaErrorInvalidValue;
 }
 
 bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,

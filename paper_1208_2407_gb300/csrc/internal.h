@@ -7,6 +7,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+struct ts_grid;
+
 namespace ts {
 
 // Error bits written by kernels into the grid's device error word.
@@ -40,6 +42,12 @@ cudaError_t launch_observe(const void *re, const void *im, const void *vplane, b
                            int nx, int ny, int64_t pitch, double J, bool norm_only,
                            double *partials, double *result, cudaStream_t st);
 
+// <phi|psi> = sum conj(phi) psi over two FP32 pitched states: result[0] real,
+// result[1] imaginary part (exact products, double-float then FP64 sums).
+cudaError_t launch_inner(const float *phi_re, const float *phi_im, const float *psi_re,
+                         const float *psi_im, int nx, int ny, int64_t pitch, double *partials,
+                         double *result, cudaStream_t st);
+
 // --- fused temporally blocked path (fused.cu) -----------------------------
 struct FusedLaunch {
     const CUtensorMap *tm_state;   // (re, im) planes of the input pair, 3-D map
@@ -51,11 +59,18 @@ struct FusedLaunch {
     // versine form (g1 = 1 - cos theta, s1); at 2 theta: lifting (t2, s2)
     float t1, s1, g1, t2, s2;
     int *err;
+    // adjoint support (launch_fused_mid only)
+    float *m_re = nullptr, *m_im = nullptr;
+    float *g_rh = nullptr, *g_rl = nullptr, *g_ih = nullptr, *g_il = nullptr;
 };
 constexpr int FUSED_MAX_K = 8;
 constexpr int FUSED_BOX_COLS = 128;   // columns a warp strip loads (box width)
 constexpr int FUSED_BOX_ROWS = 2;     // rows per pipeline slot (box height)
 cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st);
+// One step (K = 1) with the adjoint hooks: mode 1 stores the mid-step state
+// in (m_re, m_im); mode 2 is a backward step (pass the coefficients at
+// -theta) that reads the mid-step state and accumulates G.
+cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st);
 
 // Build a 3-D FP32 tensor map over two consecutive pitched planes (nx x ny
 // each, `plane_bytes` apart) for the fused path: one box load fetches the
@@ -69,5 +84,8 @@ void count_launches(int64_t n);
 
 // Record a message for ts_last_error() and return `status` (api.cu).
 int set_error(int status, const char *fmt, ...);
+
+// Drop the adjoint record of a grid that is being destroyed (adjoint.cu).
+void forget_adjoint(const ::ts_grid *g);
 
 }  // namespace ts

@@ -171,6 +171,44 @@ observe_f32_kernel(const float *__restrict__ re, const float *__restrict__ im,
     block_reduce_write<NQ>(nacc, partials);
 }
 
+// <phi|psi>: exact products, double-float per-thread sums, FP64 combine.
+__global__ void __launch_bounds__(kThreads)
+inner_f32_kernel(const float *__restrict__ ar, const float *__restrict__ ai,
+                 const float *__restrict__ br, const float *__restrict__ bi, int nx, int ny,
+                 int64_t pitch, double *__restrict__ partials)
+{
+    FF sr = ff_make(0.f), si = ff_make(0.f);
+    const int chunks_per_row = (nx + 3) / 4;
+    const int64_t nchunks = (int64_t)chunks_per_row * ny;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(c / chunks_per_row);
+        const int x0 = (int)(c - (int64_t)y * chunks_per_row) * 4;
+        const int64_t o = (int64_t)y * pitch + x0;
+        const float4 a4 = *reinterpret_cast<const float4 *>(ar + o);
+        const float4 b4 = *reinterpret_cast<const float4 *>(ai + o);
+        const float4 c4 = *reinterpret_cast<const float4 *>(br + o);
+        const float4 d4 = *reinterpret_cast<const float4 *>(bi + o);
+        const float pr[4] = {a4.x, a4.y, a4.z, a4.w}, pi[4] = {b4.x, b4.y, b4.z, b4.w};
+        const float qr[4] = {c4.x, c4.y, c4.z, c4.w}, qi[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (x0 + u >= nx) break;
+            // conj(p) q = (pr qr + pi qi) + i (pr qi - pi qr)
+            sr = ff_add(sr, ff_add(two_prod(pr[u], qr[u]), two_prod(pi[u], qi[u])));
+            si = ff_add(si, ff_add(two_prod(pr[u], qi[u]), two_prod(-pi[u], qr[u])));
+        }
+    }
+    Neu acc[2];
+    acc[0] = {0.0, 0.0};
+    acc[1] = {0.0, 0.0};
+    acc[0].add((double)sr.hi);
+    acc[0].add((double)sr.lo);
+    acc[1].add((double)si.hi);
+    acc[1].add((double)si.lo);
+    block_reduce_write<2>(acc, partials);
+}
+
 template <typename T, bool NORM_ONLY>
 __global__ void __launch_bounds__(kThreads)
 observe_kernel(const T *__restrict__ re, const T *__restrict__ im, const T *__restrict__ vp,
@@ -312,6 +350,20 @@ cudaError_t launch_observe(const void *re, const void *im, const void *vplane, b
             observe_f32_kernel<false><<<nblocks, kThreads, 0, st>>>((const float *)re, (const float *)im, (const float *)vplane, nx, ny, pitch, J_hi, J_lo, partials);
     }
     observe_finalize_kernel<<<1, kThreads, 0, st>>>(partials, nblocks, norm_only ? 1 : OBS_Q, result);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inner(const float *phi_re, const float *phi_im, const float *psi_re,
+                         const float *psi_im, int nx, int ny, int64_t pitch, double *partials,
+                         double *result, cudaStream_t st)
+{
+    const int64_t nchunks = (int64_t)((nx + 3) / 4) * ny;
+    int64_t b = (nchunks + kThreads * 8 - 1) / (kThreads * 8);
+    int nblocks = (int)(b < 1 ? 1 : (b > OBS_MAX_BLOCKS ? OBS_MAX_BLOCKS : b));
+    inner_f32_kernel<<<nblocks, kThreads, 0, st>>>(phi_re, phi_im, psi_re, psi_im, nx, ny, pitch,
+                                                   partials);
+    observe_finalize_kernel<<<1, kThreads, 0, st>>>(partials, nblocks, 2, result);
     count_launches(2);
     return cudaGetLastError();
 }

@@ -66,6 +66,12 @@ _SIGNATURES = {
     "ts_energy": [_VP, ctypes.POINTER(_DBL), _VP],
     "ts_evolve_batched": [ctypes.POINTER(_VP), _INT, ctypes.POINTER(_I64), _INT, _VP],
     "ts_norm_noalloc": [_VP, _VP, _INT, _I64, _I64, _I64, _VP, _VP],
+    "ts_adjoint_workspace": [_VP, _I64, _I64, ctypes.POINTER(ctypes.c_size_t)],
+    "ts_adjoint_forward": [_VP, _VP, _VP, _INT, _INT, _I64, _I64, _VP, ctypes.c_size_t,
+                           ctypes.POINTER(_DBL), ctypes.POINTER(_DBL), _VP],
+    "ts_adjoint_backward": [_VP, _VP, ctypes.c_size_t, _VP, _VP],
+    "ts_adjoint_grad": [_VP, _VP, _VP, _INT, _INT, _I64, _I64, _VP, ctypes.c_size_t, _VP,
+                        ctypes.POINTER(_DBL), _VP],
 }
 
 _lock = threading.Lock()
@@ -177,6 +183,33 @@ def ts_evolve_batched(handles, steps, K, stream):
     arr = (_VP * n)(*[h.value if isinstance(h, _VP) else h for h in handles])
     st = (_I64 * n)(*[int(s) for s in steps])
     _call("ts_evolve_batched", arr, n, st, K, stream)
+
+
+def ts_adjoint_workspace(h, steps, ckpt_every) -> int:
+    n = ctypes.c_size_t()
+    _call("ts_adjoint_workspace", h, steps, ckpt_every, ctypes.byref(n))
+    return int(n.value)
+
+
+def ts_adjoint_forward(h, tre_ptr, tim_ptr, dtype, where, steps, ckpt_every, ws_ptr, ws_bytes,
+                       stream):
+    F = _DBL()
+    ov = (_DBL * 2)()
+    _call("ts_adjoint_forward", h, tre_ptr, tim_ptr, dtype, where, steps, ckpt_every, ws_ptr,
+          ws_bytes, ctypes.byref(F), ov, stream)
+    return F.value, complex(ov[0], ov[1])
+
+
+def ts_adjoint_backward(h, ws_ptr, ws_bytes, grad_ptr, stream):
+    _call("ts_adjoint_backward", h, ws_ptr, ws_bytes, grad_ptr, stream)
+
+
+def ts_adjoint_grad(h, tre_ptr, tim_ptr, dtype, where, steps, ckpt_every, ws_ptr, ws_bytes,
+                    grad_ptr, stream) -> float:
+    F = _DBL()
+    _call("ts_adjoint_grad", h, tre_ptr, tim_ptr, dtype, where, steps, ckpt_every, ws_ptr,
+          ws_bytes, grad_ptr, ctypes.byref(F), stream)
+    return F.value
 
 
 def ts_norm_noalloc(re_ptr, im_ptr, dtype, nx, ny, pitch, out_ptr, stream):
@@ -327,6 +360,23 @@ class Grid:
         re, im = _VP(), _VP()
         _call("ts_grid_info", self.handle, ctypes.byref(L), ctypes.byref(re), ctypes.byref(im))
         return re.value, im.value, int(L.pitch)
+
+
+def adjoint_fidelity_grad(grid, target_re, target_im, steps: int, ckpt_every: int = 50,
+                          stream=None):
+    """(F, dF/dV) for the grid's current state and potential; the grid ends at
+    psi_T.  dF/dV is returned as an (ny, nx) float32 CUDA tensor."""
+    torch = _torch()
+    st = stream or current_stream_ptr()
+    tp, tdt, tw, keep_t = _array_ptr(target_re, grid.shape)
+    ip, idt, iw, keep_i = _array_ptr(target_im, grid.shape)
+    nbytes = ts_adjoint_workspace(grid.handle, int(steps), int(ckpt_every))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    grad = torch.empty(grid.shape, dtype=torch.float32, device="cuda")
+    F = ts_adjoint_grad(grid.handle, tp, ip, tdt, tw, int(steps), int(ckpt_every),
+                        _VP(ws.data_ptr()), nbytes, _VP(grad.data_ptr()), st)
+    del keep_t, keep_i
+    return F, grad
 
 
 def evolve_batched(grids, steps, K: int = 0, stream=None):
