@@ -180,6 +180,75 @@ ts_status ts_adjoint_grad(ts_grid *g, const void *target_re, const void *target_
                           ts_dtype target_dtype, ts_mem where, int64_t steps, int64_t ckpt_every,
                           void *ws, size_t ws_bytes, float *grad, double *fidelity, void *stream);
 
+/* Serving: a continuous-batching request loop inside the library.
+ *
+ * Each request is one evolution: an nx x ny FP32 grid, a potential V, an
+ * initial state, dt, theta (|theta| <= pi/4) and a step count.  A scheduler
+ * thread admits requests in arrival order while the device memory they hold
+ * (ts_grid_layout's slab_bytes each, FP32) fits hbm_budget_bytes and fewer
+ * than max_slots are admitted, uploads their inputs on a copy stream, and
+ * advances all admitted grids together: each epoch runs up to
+ * max_epoch_steps steps as launches of one persistent multi-grid kernel
+ * (depth K), replayed from cached CUDA graphs, so requests that arrive while
+ * others run join at the next epoch and their work overlaps on the GPU.  A
+ * request's result does not depend on what it ran with.  Finished states
+ * stay on the device until ts_server_release.
+ *
+ * Input buffers (V, psi) stay owned by the caller and must remain valid and
+ * unchanged until the request is admitted and uploaded (simplest: until it
+ * completes).  Pinned host memory keeps submission fully asynchronous;
+ * pageable memory works but stalls the scheduler during its copies.
+ * All calls are thread-safe. */
+typedef struct {
+    size_t hbm_budget_bytes;   /* device memory for admitted requests          */
+    int max_slots;             /* admitted requests at a time (1..4096)        */
+    int K;                     /* fused depth, 0 = default (4)                 */
+    int max_epoch_steps;       /* steps per epoch before re-admission, 0 = 32  */
+} ts_server_cfg;
+
+typedef struct {
+    int64_t nx, ny, steps;
+    double dt, theta;
+    const double *V;           /* nx*ny FP64, or NULL for V = 0                */
+    const void *psi_re, *psi_im;   /* initial state, nx*ny of psi_dtype        */
+    ts_dtype psi_dtype;
+    ts_mem where;              /* memory kind of V and psi                     */
+} ts_request;
+
+typedef struct {
+    int status;                /* TS_OK done, 1 pending or running, else ts_status */
+    int64_t latency_ns;        /* submission to completion                     */
+    int64_t queue_ns;          /* submission to admission                      */
+    int64_t nx, ny, steps;
+} ts_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, active, pending;
+    double p50_ms, p99_ms, mean_ms;   /* latency of completed requests          */
+    double site_steps_per_s;   /* completed sites x steps / (last completion - first submission) */
+    size_t bytes_in_use, peak_bytes;
+    int64_t epochs, graph_launches;
+} ts_server_metrics;
+
+typedef struct ts_server ts_server;
+
+ts_status ts_server_create(const ts_server_cfg *cfg, ts_server **out);
+/* TS_ERR_BUSY if the request alone exceeds the budget (it could never run). */
+ts_status ts_server_submit(ts_server *s, const ts_request *r, uint64_t *ticket);
+ts_status ts_server_poll(ts_server *s, uint64_t ticket, ts_result *out);
+/* Blocks up to timeout_ms (< 0: forever); TS_ERR_TIMEOUT if not done by then. */
+ts_status ts_server_wait(ts_server *s, uint64_t ticket, int64_t timeout_ms, ts_result *out);
+/* Copy a finished request's state out (dense, host or device).  Syncs. */
+ts_status ts_server_fetch(ts_server *s, uint64_t ticket, void *re, void *im, ts_dtype dtype,
+                          ts_mem where);
+/* Free a finished, failed or cancelled request and its device memory. */
+ts_status ts_server_release(ts_server *s, uint64_t ticket);
+/* Pending requests leave at once; running ones at the next epoch boundary. */
+ts_status ts_server_cancel(ts_server *s, uint64_t ticket);
+ts_status ts_server_stats(ts_server *s, ts_server_metrics *out);
+/* Cancels what is still queued or running, waits for the GPU, frees all. */
+ts_status ts_server_destroy(ts_server *s);
+
 /* Sum of |psi|^2 over a pitched device state, without allocating anything.
  *
  * The paper has no counterpart: this entry point exists for callers that

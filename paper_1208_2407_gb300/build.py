@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtrotter.so")
-SOURCES = ["api.cu", "plain.cu", "fused.cu", "reduce.cu", "adjoint.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "plain.cu", "fused.cu", "reduce.cu", "adjoint.cu", "server.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/trotter.h"
 #include "grid.h"
@@ -40,15 +41,151 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 size_t scratch_bytes()
 {
-    // partials, result, error word
+    // partials, result, error word, multi-grid descriptor
     return round_up(sizeof(double) * ts::OBS_MAX_BLOCKS * ts::OBS_Q, 256) +
-           round_up(sizeof(double) * ts::OBS_Q, 256) + 256;
+           round_up(sizeof(double) * ts::OBS_Q, 256) + 256 +
+           round_up(sizeof(ts::GridDesc), 256);
 }
 
 }  // namespace
 
 namespace ts {
 void count_launches(int64_t n) { g_launches += n; }
+
+ts_status grid_setup(const ts_layout &L, void *slab, bool owns_slab, ts_grid **out)
+{
+    ts_grid *g = new (std::nothrow) ts_grid();
+    if (!g) return fail(TS_ERR_OOM, "grid set-up: host allocation failed");
+    g->L = L;
+    g->esize = L.dtype == TS_F64 ? 8 : 4;
+    g->owns_slab = owns_slab;
+    g->slab = (unsigned char *)slab;
+    unsigned char *scr = g->slab + kPlanes * L.plane_bytes;
+    g->partials = (double *)scr;
+    scr += round_up(sizeof(double) * OBS_MAX_BLOCKS * OBS_Q, 256);
+    g->result = (double *)scr;
+    scr += round_up(sizeof(double) * OBS_Q, 256);
+    g->err = (int *)scr;
+    scr += 256;
+    g->desc_dev = (GridDesc *)scr;
+    g->cur = 0;
+    g->dt = g->theta = g->J = 0.0;
+    g->g1 = g->s1 = g->t1 = g->s2 = g->t2 = 0.0;
+    g->tmaps_ok = false;
+    if (L.dtype == TS_F32) {
+        const char *why = "";
+        bool ok = true;
+        for (int c = 0; c < 2 && ok; ++c)
+            ok = make_pair_tensor_map(&g->tm_state[c], g->plane(2 * c), (int)L.nx, (int)L.ny,
+                                      L.pitch, L.plane_bytes, &why);
+        ok = ok && make_pair_tensor_map(&g->tm_phase, g->pg(), (int)L.nx, (int)L.ny, L.pitch,
+                                        L.plane_bytes, &why);
+        if (!ok) {
+            delete g;
+            return fail(TS_ERR_CUDA, "grid set-up: %s", why);
+        }
+        g->tmaps_ok = true;
+    }
+    *out = g;
+    return TS_OK;
+}
+
+size_t grid_scratch_offset(const ts_layout &L) { return kPlanes * L.plane_bytes; }
+
+void grid_set_coefficients(ts_grid *g, double dt, double theta, cudaStream_t st)
+{
+    g->dt = dt;
+    g->theta = theta;
+    g->J = dt != 0.0 ? 2.0 * theta / dt : 0.0;
+    // kinetic rotation coefficients in FP64, rounded once where used:
+    // versine form (g = 1 - cos theta = 2 sin^2(theta/2), s = sin theta) and
+    // lifting form (t = tan(theta/2), s); the merged angle 2 theta in lifting form
+    const double sh1 = std::sin(0.5 * theta);
+    g->g1 = 2.0 * sh1 * sh1;
+    g->s1 = std::sin(theta);
+    g->t1 = std::tan(0.5 * theta);
+    g->s2 = std::sin(2.0 * theta);
+    g->t2 = std::tan(theta);
+    if (!g->f64()) grid_write_desc(g, st);
+}
+
+void grid_write_desc(ts_grid *g, cudaStream_t st)
+{
+    GridDesc &d = g->desc_host;
+    d.tm_state[0] = g->tm_state[0];
+    d.tm_state[1] = g->tm_state[1];
+    d.tm_phase = g->tm_phase;
+    for (int c = 0; c < 2; ++c) {
+        d.re[c] = (float *)g->plane(2 * c);
+        d.im[c] = (float *)g->plane(2 * c + 1);
+    }
+    d.nx = (int)g->L.nx;
+    d.ny = (int)g->L.ny;
+    d.pitch = g->L.pitch;
+    d.t1 = (float)g->t1;
+    d.s1 = (float)g->s1;
+    d.g1 = (float)g->g1;
+    d.t2 = (float)g->t2;
+    d.s2 = (float)g->s2;
+    // pageable source: the call returns once the host struct is staged, and
+    // the device copy lands in stream order before later kernels read it
+    cudaMemcpyAsync(g->desc_dev, &d, sizeof(GridDesc), cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t evolve_multi(ts_grid *const *gs, const int64_t *steps, int n, int K, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    // Each grid runs floor(steps/K) launches at depth K, then one at depth
+    // steps % K -- the same sequence as evolving it alone.  All grids with a
+    // launch left share each launch; a table is rebuilt when the set changes.
+    std::vector<int64_t> full(n), rem(n);
+    int64_t max_full = 0;
+    for (int i = 0; i < n; ++i) {
+        full[i] = steps[i] / K;
+        rem[i] = steps[i] % K;
+        if (full[i] > max_full) max_full = full[i];
+    }
+    EpochEntry *tab = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&tab, sizeof(EpochEntry) * (size_t)n, st);
+    if (e != cudaSuccess) return e;
+    std::vector<EpochEntry> h;
+    auto run = [&](int depth, const std::vector<int> &idx, int64_t launches) -> cudaError_t {
+        h.clear();
+        int64_t units = 0;
+        for (int i : idx) {
+            h.push_back(EpochEntry{gs[i]->desc_dev, units, gs[i]->cur, 0});
+            units += fused_units(depth, (int)gs[i]->L.nx, (int)gs[i]->L.ny);
+        }
+        cudaError_t err = cudaMemcpyAsync(tab, h.data(), sizeof(EpochEntry) * h.size(),
+                                          cudaMemcpyHostToDevice, st);
+        for (int64_t t = 0; t < launches && err == cudaSuccess; ++t)
+            err = launch_fused_multi(depth, tab, (int)h.size(), units, (int)(t & 1),
+                                     gs[idx[0]]->err, st);
+        if (err == cudaSuccess && (launches & 1))
+            for (int i : idx) gs[i]->cur ^= 1;
+        return err;
+    };
+    int64_t done = 0;
+    while (e == cudaSuccess && done < max_full) {
+        std::vector<int> idx;
+        int64_t until = max_full;
+        for (int i = 0; i < n; ++i)
+            if (full[i] > done) {
+                idx.push_back(i);
+                if (full[i] < until) until = full[i];
+            }
+        e = run(K, idx, until - done);
+        done = until;
+    }
+    for (int r = 1; r < K && e == cudaSuccess; ++r) {
+        std::vector<int> idx;
+        for (int i = 0; i < n; ++i)
+            if (rem[i] == r) idx.push_back(i);
+        if (!idx.empty()) e = run(r, idx, 1);
+    }
+    cudaError_t f = cudaFreeAsync(tab, st);
+    return e != cudaSuccess ? e : f;
+}
 
 int set_error(int status, const char *fmt, ...)
 {
@@ -104,52 +241,29 @@ ts_status ts_create_grid(int64_t nx, int64_t ny, ts_dtype dtype, void *slab, siz
             return fail(TS_ERR_ARG, "ts_create_grid: slab has %zu bytes, needs %zu", slab_bytes,
                         L.slab_bytes);
     }
-    ts_grid *g = new (std::nothrow) ts_grid();
-    if (!g) return fail(TS_ERR_OOM, "ts_create_grid: host allocation failed");
-    g->L = L;
-    g->esize = dtype == TS_F64 ? 8 : 4;
-    g->owns_slab = slab == nullptr;
-    if (g->owns_slab) {
-        cudaError_t e = cudaMalloc((void **)&g->slab, L.slab_bytes);
+    bool owns = slab == nullptr;
+    if (owns) {
+        cudaError_t e = cudaMalloc(&slab, L.slab_bytes);
         if (e != cudaSuccess) {
-            delete g;
             cudaGetLastError();
             return fail(TS_ERR_OOM, "ts_create_grid: cudaMalloc(%zu): %s", L.slab_bytes,
                         cudaGetErrorString(e));
         }
-    } else {
-        g->slab = (unsigned char *)slab;
+    }
+    ts_grid *g = nullptr;
+    st = ts::grid_setup(L, slab, owns, &g);
+    if (st != TS_OK) {
+        if (owns) cudaFree(slab);
+        return st;
     }
     cudaError_t e = cudaMemset(g->slab, 0, L.slab_bytes);
-    if (e != cudaSuccess) {
-        if (g->owns_slab) cudaFree(g->slab);
-        delete g;
-        return cuda_fail(e, "ts_create_grid: zero-fill");
+    if (e == cudaSuccess && !g->f64()) {
+        ts::grid_write_desc(g, nullptr);
+        e = cudaStreamSynchronize(nullptr);
     }
-    unsigned char *scr = g->slab + kPlanes * L.plane_bytes;
-    g->partials = (double *)scr;
-    scr += round_up(sizeof(double) * ts::OBS_MAX_BLOCKS * ts::OBS_Q, 256);
-    g->result = (double *)scr;
-    scr += round_up(sizeof(double) * ts::OBS_Q, 256);
-    g->err = (int *)scr;
-    g->cur = 0;
-    g->dt = g->theta = g->J = 0.0;
-    g->g1 = g->s1 = g->t1 = g->s2 = g->t2 = 0.0;
-    g->tmaps_ok = false;
-    if (dtype == TS_F32) {
-        const char *why = "";
-        bool ok = true;
-        for (int c = 0; c < 2 && ok; ++c)
-            ok = ts::make_pair_tensor_map(&g->tm_state[c], g->plane(2 * c), (int)nx, (int)ny,
-                                          L.pitch, L.plane_bytes, &why);
-        ok = ok && ts::make_pair_tensor_map(&g->tm_phase, g->pg(), (int)nx, (int)ny, L.pitch,
-                                            L.plane_bytes, &why);
-        if (!ok) {
-            if (g->owns_slab) cudaFree(g->slab);
-            delete g;
-            return fail(TS_ERR_CUDA, "ts_create_grid: %s", why);
-        }
-        g->tmaps_ok = true;
+    if (e != cudaSuccess) {
+        ts_destroy_grid(g);
+        return cuda_fail(e, "ts_create_grid: zero-fill");
     }
     *out = g;
     return TS_OK;
@@ -309,18 +423,7 @@ ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
     if (where != TS_HOST && where != TS_DEVICE)
         return fail(TS_ERR_ARG, "ts_set_potential: unknown memory kind");
     cudaStream_t st = (cudaStream_t)stream;
-    g->dt = dt;
-    g->theta = theta;
-    g->J = dt != 0.0 ? 2.0 * theta / dt : 0.0;
-    // kinetic rotation coefficients in FP64, rounded once where used:
-    // versine form (g = 1 - cos theta = 2 sin^2(theta/2), s = sin theta) and
-    // lifting form (t = tan(theta/2), s); the merged angle 2 theta in lifting form
-    const double sh1 = std::sin(0.5 * theta);
-    g->g1 = 2.0 * sh1 * sh1;
-    g->s1 = std::sin(theta);
-    g->t1 = std::tan(0.5 * theta);
-    g->s2 = std::sin(2.0 * theta);
-    g->t2 = std::tan(theta);
+    ts::grid_set_coefficients(g, dt, theta, st);
     const int nx = (int)g->L.nx, ny = (int)g->L.ny;
     cudaError_t e;
     if (!V) {
@@ -434,10 +537,26 @@ ts_status ts_evolve_plain(ts_grid *g, int64_t steps, void *stream)
 ts_status ts_evolve_batched(ts_grid *const *gs, int n, const int64_t *steps, int K, void *stream)
 {
     if (n < 0 || (n > 0 && (!gs || !steps))) return fail(TS_ERR_ARG, "ts_evolve_batched: bad arguments");
+    if (K < 0 || K > ts::FUSED_MAX_K) return fail(TS_ERR_ARG, "ts_evolve_batched: K must be in [0, 8]");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int depth = K == 0 ? auto_depth() : K;
+    // grids the multi-grid kernel can take: FP32, |theta| <= pi/4; the rest
+    // evolve one by one
+    std::vector<ts_grid *> multi;
+    std::vector<int64_t> msteps;
     for (int i = 0; i < n; ++i) {
-        ts_status s = ts_evolve(gs[i], steps[i], K, stream);
-        if (s != TS_OK) return s;
+        if (!gs[i] || steps[i] < 0) return fail(TS_ERR_ARG, "ts_evolve_batched: grid %d", i);
+        if (steps[i] == 0) continue;
+        if (gs[i]->f64() || std::fabs(gs[i]->theta) > 0.25 * M_PI) {
+            ts_status s = ts_evolve(gs[i], steps[i], K, stream);
+            if (s != TS_OK) return s;
+        } else {
+            multi.push_back(gs[i]);
+            msteps.push_back(steps[i]);
+        }
     }
+    cudaError_t e = ts::evolve_multi(multi.data(), msteps.data(), (int)multi.size(), depth, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ts_evolve_batched: multi-grid launch");
     return TS_OK;
 }
 

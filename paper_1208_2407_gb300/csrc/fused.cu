@@ -169,6 +169,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     return true;
 }
 
+// Make a tensor map that was written to global memory before this launch
+// visible to the TMA unit (its descriptor cache is not coherent with writes).
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *tm)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(tm))
+                 : "memory");
+}
+
 // One box of two planes: x in [x, x+128), rows y, y+1, planes 0 and 1.
 __device__ __forceinline__ void tma_load_pair(void *dst, const CUtensorMap *tm, int x, int y,
                                               uint64_t *bar)
@@ -434,158 +443,239 @@ __device__ __forceinline__ void pipeline_step(Frag (&carry)[2 * K], Frag a, Frag
     x_even(O1, c.E1);
 }
 
+// A warp's two slot rings: barriers, buffers, and the ring positions and
+// mbarrier phase parities of the next row pair to be consumed (they carry
+// over from one row range to the next).
+struct WarpRings {
+    uint64_t *bar_s, *bar_p;
+    unsigned char *ring_s, *ring_p;
+    int pos_s, pos_p;
+    uint32_t par_s, par_p;
+};
+
+template <int K>
+__device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int warp, int lane)
+{
+    using C = Cfg<K>;
+    constexpr int NSS = C::NSS, NSP = C::NSP;
+    WarpRings r;
+    // barriers first, then 1 KiB-aligned slots (state ring, phase ring)
+    r.bar_s = reinterpret_cast<uint64_t *>(smem_raw) + warp * (NSS + NSP);
+    r.bar_p = r.bar_s + NSS;
+    const uint32_t base_addr = smem_addr(smem_raw);
+    const uint32_t slots_off =
+        ((base_addr + C::WPC * (NSS + NSP) * 8 + 1023u) & ~1023u) - base_addr;
+    r.ring_s = smem_raw + slots_off + (size_t)warp * C::WARP_SMEM;
+    r.ring_p = r.ring_s + NSS * SLOT_BYTES;
+    r.pos_s = r.pos_p = 0;
+    r.par_s = r.par_p = 0;
+    if (lane == 0) {
+        for (int i = 0; i < NSS + NSP; ++i) mbar_init(&r.bar_s[i], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    return r;
+}
+
+// Stream the row pairs [q0, q1) of strip sx of one grid through the K-step
+// pipeline: rows [2 q0, 2 q1) are written to (p.out_re, p.out_im).  Returns
+// false if a bounded wait gave up (the error bit is set and this warp's
+// outstanding copies are drained).
+template <int K, int MODE>
+__device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_state,
+                                            const CUtensorMap *tm_phase, const KParams &p,
+                                            int sx, int q0, int q1, int lane)
+{
+    using C = Cfg<K>;
+    constexpr int NSS = C::NSS, NSP = C::NSP, HALO = C::HALO, VALID = C::VALID;
+    const int XL = sx * VALID - HALO;              // first loaded column (multiple of 4)
+    const int xg = XL + 4 * lane;                  // this lane's first column
+    const int Y0 = 2 * q0, Y1 = 2 * q1;            // output rows [Y0, Y1)
+    const int Ys = Y0 - 2 * K;                     // first loaded row
+    const int n_iter = (Y1 - Y0) / 2 + 2 * K;      // row pairs loaded
+
+    // pair (x, x+1) is rotated iff both sites are on the grid
+    auto xok = [&](int x) { return x >= 0 && x + 1 < p.nx; };
+    const bool e0 = xok(xg), e1 = xok(xg + 2), o0 = xok(xg + 1), oR = xok(xg + 3),
+               oL = xok(xg - 1);
+    StripCoef c;
+    c.E1 = {e0 ? p.t1 : 0.f, e0 ? p.s1 : 0.f, e1 ? p.t1 : 0.f, e1 ? p.s1 : 0.f};
+    c.E2 = {e0 ? p.t2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.t2 : 0.f, e1 ? p.s2 : 0.f};
+    c.O = {o0 ? p.t1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
+           oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
+    const bool store_lane = lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
+    const Owned own = {Y0, Y1, xg, store_lane};
+
+    // lane 0 only: fill ring position `pos` with row pair j
+    auto issue_state = [&](int pos, int j) {
+        mbar_expect_tx(&r.bar_s[pos], SLOT_BYTES);
+        tma_load_pair(r.ring_s + pos * SLOT_BYTES, tm_state, XL, Ys + 2 * j, &r.bar_s[pos]);
+    };
+    auto issue_phase = [&](int pos, int j) {
+        mbar_expect_tx(&r.bar_p[pos], SLOT_BYTES);
+        tma_load_pair(r.ring_p + pos * SLOT_BYTES, tm_phase, XL, Ys + 2 * j, &r.bar_p[pos]);
+    };
+    const int n_pro_s = n_iter < NSS ? n_iter : NSS;
+    const int n_pro_p = n_iter < NSP ? n_iter : NSP;
+    if (lane == 0) {
+        fence_proxy_async();
+        for (int j = 0; j < n_pro_p; ++j) {
+            if (j < n_pro_s) issue_state((r.pos_s + j) % NSS, j);
+            issue_phase((r.pos_p + j) % NSP, j);
+        }
+    }
+    int issued_s = n_pro_s, issued_p = n_pro_p;
+
+    Frag carry[2 * K];
+#pragma unroll
+    for (int i = 0; i < 2 * K; ++i) carry[i] = zero_frag();
+
+#pragma unroll ROW_LOOP_UNROLL
+    for (int j = 0; j < n_iter; ++j) {
+        bool ok = mbar_wait(&r.bar_s[r.pos_s], r.par_s, WAIT_LIMIT_NS) &&
+                  mbar_wait(&r.bar_p[r.pos_p], r.par_p, WAIT_LIMIT_NS);
+        ok = __all_sync(FULL, ok);
+        if (!ok) {
+            if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
+            // drain this warp's outstanding copies (bounded) before leaving
+            for (int jj = j, ps = r.pos_s, ph = r.par_s; jj < issued_s; ++jj) {
+                mbar_wait(&r.bar_s[ps], ph, WAIT_LIMIT_NS / 4);
+                if (++ps == NSS) { ps = 0; ph ^= 1u; }
+            }
+            for (int jj = j, ps = r.pos_p, ph = r.par_p; jj < issued_p; ++jj) {
+                mbar_wait(&r.bar_p[ps], ph, WAIT_LIMIT_NS / 4);
+                if (++ps == NSP) { ps = 0; ph ^= 1u; }
+            }
+            return false;
+        }
+        const unsigned char *sj = r.ring_s + r.pos_s * SLOT_BYTES;
+        Frag a, b;
+        a.re = lds4(sj, 0, 0, lane);
+        a.im = lds4(sj, 1, 0, lane);
+        b.re = lds4(sj, 0, 1, lane);
+        b.im = lds4(sj, 1, 1, lane);
+        const int yin = Ys + 2 * j;
+        Frag O0, O1;
+        const bool interior = j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny;
+        if (interior)
+            pipeline_step<K, true, MODE>(carry, a, b, yin, j, r.ring_p, r.pos_p, c, p, lane, own,
+                                         O0, O1);
+        else
+            pipeline_step<K, false, MODE>(carry, a, b, yin, j, r.ring_p, r.pos_p, c, p, lane, own,
+                                          O0, O1);
+
+        const int yo = yin - 2 * K;
+        if (store_lane && yo >= Y0 && yo < Y1) {
+            float *rr = p.out_re + (int64_t)yo * p.pitch + xg;
+            float *mm = p.out_im + (int64_t)yo * p.pitch + xg;
+            if (yo < p.ny) {
+                *reinterpret_cast<float4 *>(rr) = O0.re;
+                *reinterpret_cast<float4 *>(mm) = O0.im;
+            }
+            if (yo + 1 < p.ny) {
+                *reinterpret_cast<float4 *>(rr + p.pitch) = O1.re;
+                *reinterpret_cast<float4 *>(mm + p.pitch) = O1.im;
+            }
+        }
+
+        // state slot j and phase slot j-K are no longer read: refill them
+        // with row pairs j + NSS and j - K + NSP (the same ring positions)
+        __syncwarp();
+        const int js = j + NSS, jp = j - K + NSP;
+        const bool more_s = js < n_iter, more_p = j >= K && jp < n_iter;
+        if (lane == 0 && (more_s || more_p)) {
+            fence_proxy_async();
+            if (more_s) issue_state(r.pos_s, js);
+            if (more_p) issue_phase(r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
+        }
+        issued_s += more_s;
+        issued_p += more_p;
+        if (++r.pos_s == NSS) { r.pos_s = 0; r.par_s ^= 1u; }
+        if (++r.pos_p == NSP) { r.pos_p = 0; r.par_p ^= 1u; }
+    }
+    __syncwarp();
+    return true;
+}
+
+// One grid; the (strip, row-pair) units are split into equal contiguous
+// ranges, one per warp of a persistent launch.
 template <int K, int MODE>
 __global__ void __launch_bounds__(Cfg<K>::WPC * 32, TS_FUSED_MIN_BLOCKS)
 fused_kernel(const __grid_constant__ CUtensorMap tm_state,
              const __grid_constant__ CUtensorMap tm_phase, const KParams p)
 {
-    using C = Cfg<K>;
-    constexpr int NSS = C::NSS, NSP = C::NSP, HALO = C::HALO, VALID = C::VALID;
-    constexpr int WARPS_PER_CTA = C::WPC;
-
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * WARPS_PER_CTA + warp;
+    const int gw = blockIdx.x * Cfg<K>::WPC + warp;
     if (gw >= p.total_warps) return;
-
-    // carve: barriers first, then 1 KiB-aligned slots (state ring, phase ring)
-    uint64_t *bar_s = reinterpret_cast<uint64_t *>(smem_raw) + warp * (NSS + NSP);
-    uint64_t *bar_p = bar_s + NSS;
-    const uint32_t base_addr = smem_addr(smem_raw);
-    const uint32_t slots_off =
-        ((base_addr + WARPS_PER_CTA * (NSS + NSP) * 8 + 1023u) & ~1023u) - base_addr;
-    unsigned char *ring_s = smem_raw + slots_off + (size_t)warp * C::WARP_SMEM;
-    unsigned char *ring_p = ring_s + NSS * SLOT_BYTES;
-
-    if (lane == 0) {
-        for (int i = 0; i < NSS + NSP; ++i) mbar_init(&bar_s[i], 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
-
+    WarpRings r = carve_rings<K>(smem_raw, warp, lane);
     const int64_t u_begin = (int64_t)gw * p.units / p.total_warps;
     const int64_t u_end = (int64_t)(gw + 1) * p.units / p.total_warps;
-    // ring positions and mbarrier phase parities of the next row pair to be
-    // consumed; they carry over from one row range to the next
-    int pos_s = 0, pos_p = 0;
-    uint32_t par_s = 0, par_p = 0;
-    bool failed = false;
-
-    for (int64_t u = u_begin; u < u_end && !failed;) {
+    for (int64_t u = u_begin; u < u_end;) {
         const int sx = (int)(u / p.n_pairs);
         const int q0 = (int)(u - (int64_t)sx * p.n_pairs);
         const int64_t q1_want = (int64_t)q0 + (u_end - u);
         const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
         u += q1 - q0;
+        if (!run_segment<K, MODE>(r, &tm_state, &tm_phase, p, sx, q0, q1, lane)) return;
+    }
+}
 
-        const int XL = sx * VALID - HALO;              // first loaded column (multiple of 4)
-        const int xg = XL + 4 * lane;                  // this lane's first column
-        const int Y0 = 2 * q0, Y1 = 2 * q1;            // output rows [Y0, Y1)
-        const int Ys = Y0 - 2 * K;                     // first loaded row
-        const int n_iter = (Y1 - Y0) / 2 + 2 * K;      // row pairs loaded
-
-        // pair (x, x+1) is rotated iff both sites are on the grid
-        auto xok = [&](int x) { return x >= 0 && x + 1 < p.nx; };
-        const bool e0 = xok(xg), e1 = xok(xg + 2), o0 = xok(xg + 1), oR = xok(xg + 3),
-                   oL = xok(xg - 1);
-        StripCoef c;
-        c.E1 = {e0 ? p.t1 : 0.f, e0 ? p.s1 : 0.f, e1 ? p.t1 : 0.f, e1 ? p.s1 : 0.f};
-        c.E2 = {e0 ? p.t2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.t2 : 0.f, e1 ? p.s2 : 0.f};
-        c.O = {o0 ? p.t1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
-               oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
-        const bool store_lane =
-            lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
-        const Owned own = {Y0, Y1, xg, store_lane};
-
-        // lane 0 only: fill ring position `pos` with row pair j
-        auto issue_state = [&](int pos, int j) {
-            mbar_expect_tx(&bar_s[pos], SLOT_BYTES);
-            tma_load_pair(ring_s + pos * SLOT_BYTES, &tm_state, XL, Ys + 2 * j, &bar_s[pos]);
-        };
-        auto issue_phase = [&](int pos, int j) {
-            mbar_expect_tx(&bar_p[pos], SLOT_BYTES);
-            tma_load_pair(ring_p + pos * SLOT_BYTES, &tm_phase, XL, Ys + 2 * j, &bar_p[pos]);
-        };
-        const int n_pro_s = n_iter < NSS ? n_iter : NSS;
-        const int n_pro_p = n_iter < NSP ? n_iter : NSP;
-        if (lane == 0) {
-            fence_proxy_async();
-            for (int j = 0; j < n_pro_p; ++j) {
-                if (j < n_pro_s) issue_state((pos_s + j) % NSS, j);
-                issue_phase((pos_p + j) % NSP, j);
+// Many grids in one persistent launch (the serving path): the units of all
+// the grids of an epoch table, concatenated in table order, are split into
+// equal contiguous ranges, one per warp.  A grid's tensor maps live in its
+// descriptor in global memory, written once when the grid was set up.
+template <int K>
+__global__ void __launch_bounds__(Cfg<K>::WPC * 32, TS_FUSED_MIN_BLOCKS)
+fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t total_units,
+                   int total_warps, int flip, int *err)
+{
+    using C = Cfg<K>;
+    extern __shared__ unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * C::WPC + warp;
+    if (gw >= total_warps) return;
+    WarpRings r = carve_rings<K>(smem_raw, warp, lane);
+    const int64_t u_begin = (int64_t)gw * total_units / total_warps;
+    const int64_t u_end = (int64_t)(gw + 1) * total_units / total_warps;
+    int gi = 0, fenced = -1;
+    for (int64_t u = u_begin; u < u_end;) {
+        while (gi + 1 < n_grids && tab[gi + 1].unit_begin <= u) ++gi;
+        const EpochEntry e = tab[gi];
+        const GridDesc *d = e.desc;
+        const int cur = e.cur0 ^ flip;
+        if (fenced != gi) {
+            if (lane == 0) {
+                tensormap_acquire(&d->tm_state[cur]);
+                tensormap_acquire(&d->tm_phase);
             }
-        }
-        int issued_s = n_pro_s, issued_p = n_pro_p;
-
-        Frag carry[2 * K];
-#pragma unroll
-        for (int i = 0; i < 2 * K; ++i) carry[i] = zero_frag();
-
-#pragma unroll ROW_LOOP_UNROLL
-        for (int j = 0; j < n_iter; ++j) {
-            bool ok = mbar_wait(&bar_s[pos_s], par_s, WAIT_LIMIT_NS) &&
-                      mbar_wait(&bar_p[pos_p], par_p, WAIT_LIMIT_NS);
-            ok = __all_sync(FULL, ok);
-            if (!ok) {
-                failed = true;
-                if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
-                // drain this warp's outstanding copies (bounded) before leaving
-                for (int jj = j, ps = pos_s, ph = par_s; jj < issued_s; ++jj) {
-                    mbar_wait(&bar_s[ps], ph, WAIT_LIMIT_NS / 4);
-                    if (++ps == NSS) { ps = 0; ph ^= 1u; }
-                }
-                for (int jj = j, ps = pos_p, ph = par_p; jj < issued_p; ++jj) {
-                    mbar_wait(&bar_p[ps], ph, WAIT_LIMIT_NS / 4);
-                    if (++ps == NSP) { ps = 0; ph ^= 1u; }
-                }
-                break;
-            }
-            const unsigned char *sj = ring_s + pos_s * SLOT_BYTES;
-            Frag a, b;
-            a.re = lds4(sj, 0, 0, lane);
-            a.im = lds4(sj, 1, 0, lane);
-            b.re = lds4(sj, 0, 1, lane);
-            b.im = lds4(sj, 1, 1, lane);
-            const int yin = Ys + 2 * j;
-            Frag O0, O1;
-            const bool interior = j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny;
-            if (interior)
-                pipeline_step<K, true, MODE>(carry, a, b, yin, j, ring_p, pos_p, c, p, lane, own,
-                                             O0, O1);
-            else
-                pipeline_step<K, false, MODE>(carry, a, b, yin, j, ring_p, pos_p, c, p, lane, own,
-                                              O0, O1);
-
-            const int yo = yin - 2 * K;
-            if (store_lane && yo >= Y0 && yo < Y1) {
-                float *r = p.out_re + (int64_t)yo * p.pitch + xg;
-                float *m = p.out_im + (int64_t)yo * p.pitch + xg;
-                if (yo < p.ny) {
-                    *reinterpret_cast<float4 *>(r) = O0.re;
-                    *reinterpret_cast<float4 *>(m) = O0.im;
-                }
-                if (yo + 1 < p.ny) {
-                    *reinterpret_cast<float4 *>(r + p.pitch) = O1.re;
-                    *reinterpret_cast<float4 *>(m + p.pitch) = O1.im;
-                }
-            }
-
-            // state slot j and phase slot j-K are no longer read: refill them
-            // with row pairs j + NSS and j - K + NSP (the same ring positions)
             __syncwarp();
-            const int js = j + NSS, jp = j - K + NSP;
-            const bool more_s = js < n_iter, more_p = j >= K && jp < n_iter;
-            if (lane == 0 && (more_s || more_p)) {
-                fence_proxy_async();
-                if (more_s) issue_state(pos_s, js);
-                if (more_p) issue_phase(pos_p - K < 0 ? pos_p - K + NSP : pos_p - K, jp);
-            }
-            issued_s += more_s;
-            issued_p += more_p;
-            if (++pos_s == NSS) { pos_s = 0; par_s ^= 1u; }
-            if (++pos_p == NSP) { pos_p = 0; par_p ^= 1u; }
+            fenced = gi;
         }
-        __syncwarp();
+        KParams p;
+        p.nx = d->nx;
+        p.ny = d->ny;
+        p.pitch = d->pitch;
+        p.out_re = d->re[cur ^ 1];
+        p.out_im = d->im[cur ^ 1];
+        p.t1 = d->t1;
+        p.s1 = d->s1;
+        p.g1 = d->g1;
+        p.t2 = d->t2;
+        p.s2 = d->s2;
+        p.err = err;
+        p.n_pairs = (p.ny + 1) / 2;
+        const int64_t local = u - e.unit_begin;
+        const int64_t g_units = (gi + 1 < n_grids ? tab[gi + 1].unit_begin : total_units) -
+                                e.unit_begin;
+        const int sx = (int)(local / p.n_pairs);
+        const int q0 = (int)(local - (int64_t)sx * p.n_pairs);
+        int64_t q1_want = (int64_t)q0 + (u_end - u);
+        const int64_t left_in_grid = g_units - local;
+        if (q1_want > q0 + left_in_grid) q1_want = q0 + left_in_grid;
+        const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
+        u += q1 - q0;
+        if (!run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, p, sx, q0, q1, lane)) return;
     }
 }
 
@@ -651,6 +741,91 @@ cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st)
     case 6: return launch_k<6, 0>(a, st);
     case 7: return launch_k<7, 0>(a, st);
     case 8: return launch_k<8, 0>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int64_t fused_units(int K, int nx, int ny)
+{
+    const int halo = ((2 * K + 3) / 4) * 4;
+    const int valid = FUSED_BOX_COLS - 2 * halo;
+    return (int64_t)((nx + valid - 1) / valid) * ((ny + 1) / 2);
+}
+
+template <int K>
+struct MultiOcc {
+    static int blocks_per_sm, num_sms;
+};
+template <int K> int MultiOcc<K>::blocks_per_sm = -1;
+template <int K> int MultiOcc<K>::num_sms = 0;
+
+template <int K>
+cudaError_t prepare_multi_k()
+{
+    using C = Cfg<K>;
+    int &blocks_per_sm = MultiOcc<K>::blocks_per_sm;
+    int &num_sms = MultiOcc<K>::num_sms;
+    if (blocks_per_sm < 0) {
+        cudaError_t e = cudaFuncSetAttribute(fused_multi_kernel<K>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fused_multi_kernel<K>,
+                                                          C::WPC * 32, C::SMEM);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    return cudaSuccess;
+}
+
+template <int K>
+cudaError_t launch_multi_k(const EpochEntry *tab, int n_grids, int64_t total_units, int flip,
+                           int *err, cudaStream_t st)
+{
+    using C = Cfg<K>;
+    cudaError_t pe = prepare_multi_k<K>();
+    if (pe != cudaSuccess) return pe;
+    const int blocks_per_sm = MultiOcc<K>::blocks_per_sm, num_sms = MultiOcc<K>::num_sms;
+    int64_t want = (total_units + 15) / 16;
+    int64_t cap = (int64_t)num_sms * blocks_per_sm * C::WPC;
+    const int total_warps = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    const int blocks = (total_warps + C::WPC - 1) / C::WPC;
+    fused_multi_kernel<K><<<blocks, C::WPC * 32, C::SMEM, st>>>(tab, n_grids, total_units,
+                                                               total_warps, flip, err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t fused_multi_prepare(int K)
+{
+    switch (K) {
+    case 1: return prepare_multi_k<1>();
+    case 2: return prepare_multi_k<2>();
+    case 3: return prepare_multi_k<3>();
+    case 4: return prepare_multi_k<4>();
+    case 5: return prepare_multi_k<5>();
+    case 6: return prepare_multi_k<6>();
+    case 7: return prepare_multi_k<7>();
+    case 8: return prepare_multi_k<8>();
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, int64_t total_units,
+                               int flip, int *err, cudaStream_t st)
+{
+    if (n_grids < 1 || total_units < 1) return cudaSuccess;
+    switch (K) {
+    case 1: return launch_multi_k<1>(tab, n_grids, total_units, flip, err, st);
+    case 2: return launch_multi_k<2>(tab, n_grids, total_units, flip, err, st);
+    case 3: return launch_multi_k<3>(tab, n_grids, total_units, flip, err, st);
+    case 4: return launch_multi_k<4>(tab, n_grids, total_units, flip, err, st);
+    case 5: return launch_multi_k<5>(tab, n_grids, total_units, flip, err, st);
+    case 6: return launch_multi_k<6>(tab, n_grids, total_units, flip, err, st);
+    case 7: return launch_multi_k<7>(tab, n_grids, total_units, flip, err, st);
+    case 8: return launch_multi_k<8>(tab, n_grids, total_units, flip, err, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -6,6 +6,7 @@
 #include <cuda.h>
 
 #include "../../include/trotter.h"
+#include "internal.h"
 
 // One grid: a slab of seven planes (re, im of ping-pong pairs 0 and 1,
 // gamma_V, s_V, V) plus reduction scratch; see ts_grid_layout.
@@ -21,6 +22,8 @@ struct ts_grid {
     int *err;
     bool tmaps_ok;
     CUtensorMap tm_state[2], tm_phase;   // (re, im) of pair 0 / 1; (gamma_V, s_V)
+    ts::GridDesc *desc_dev;              // the same, for multi-grid launches (in the slab)
+    ts::GridDesc desc_host;
 
     void *plane(int i) const { return slab + (size_t)i * L.plane_bytes; }
     void *re() const { return plane(2 * cur); }
@@ -33,3 +36,19 @@ struct ts_grid {
     bool f64() const { return L.dtype == TS_F64; }
 };
 
+
+namespace ts {
+// Fill a grid handle for a caller-provided slab (tensor maps included) with
+// no device work; ts_create_grid adds the zero-fill (api.cu).
+ts_status grid_setup(const ts_layout &L, void *slab, bool owns_slab, ts_grid **out);
+// Byte offset of the scratch area (partials, result, error word, descriptor).
+size_t grid_scratch_offset(const ts_layout &L);
+// Rotation coefficients for (dt, theta), and the descriptor (api.cu).
+void grid_set_coefficients(ts_grid *g, double dt, double theta, cudaStream_t st);
+// Write the grid's multi-grid descriptor (tensor maps, planes, coefficients)
+// into its slab on stream st (api.cu).
+void grid_write_desc(ts_grid *g, cudaStream_t st);
+// Evolve n FP32 grids (|theta| <= pi/4) together with the multi-grid kernel
+// at depth K (api.cu).
+cudaError_t evolve_multi(ts_grid *const *gs, const int64_t *steps, int n, int K, cudaStream_t st);
+}  // namespace ts

@@ -72,6 +72,36 @@ cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st);
 // -theta) that reads the mid-step state and accumulates G.
 cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st);
 
+// Device-resident description of one FP32 grid for the multi-grid launch
+// (written once per grid set-up; read by the kernel with generic loads, its
+// tensor maps by TMA).
+struct GridDesc {
+    CUtensorMap tm_state[2];   // (re, im) of pair 0 / pair 1
+    CUtensorMap tm_phase;      // (gamma_V, s_V)
+    float *re[2], *im[2];      // planes of pair 0 / pair 1
+    int nx, ny;
+    int64_t pitch;
+    float t1, s1, g1, t2, s2;  // rotation coefficients (see FusedLaunch)
+};
+
+// One grid of an epoch: its descriptor, the first of its units in the
+// concatenated unit list, and which pair holds its state at flip = 0.
+struct EpochEntry {
+    const GridDesc *desc;
+    int64_t unit_begin;
+    int cur0;
+    int pad;
+};
+
+// Set the multi-grid kernel's attributes for depth K (call outside stream capture).
+cudaError_t fused_multi_prepare(int K);
+// Units (strip x row-pair work items) of an nx x ny grid at depth K.
+int64_t fused_units(int K, int nx, int ny);
+// K steps for every grid of a device epoch table; the input pair of grid i
+// is tab[i].cur0 ^ flip.
+cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, int64_t total_units,
+                               int flip, int *err, cudaStream_t st);
+
 // Build a 3-D FP32 tensor map over two consecutive pitched planes (nx x ny
 // each, `plane_bytes` apart) for the fused path: one box load fetches the
 // same rows of both planes.  Returns false (and a message) if the driver

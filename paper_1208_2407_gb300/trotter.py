@@ -45,6 +45,34 @@ class ts_observables(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("norm", "x", "y", "x2", "y2", "e_kin", "e_pot")]
 
 
+class ts_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
+                ("K", ctypes.c_int), ("max_epoch_steps", ctypes.c_int)]
+
+
+class ts_request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("dt", ctypes.c_double), ("theta", ctypes.c_double),
+                ("V", ctypes.c_void_p), ("psi_re", ctypes.c_void_p), ("psi_im", ctypes.c_void_p),
+                ("psi_dtype", ctypes.c_int), ("where", ctypes.c_int)]
+
+
+class ts_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("latency_ns", ctypes.c_int64),
+                ("queue_ns", ctypes.c_int64), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("steps", ctypes.c_int64)]
+
+
+class ts_server_metrics(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("site_steps_per_s", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("epochs", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64)]
+
+
 _VP = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _INT = ctypes.c_int
@@ -72,6 +100,15 @@ _SIGNATURES = {
     "ts_adjoint_backward": [_VP, _VP, ctypes.c_size_t, _VP, _VP],
     "ts_adjoint_grad": [_VP, _VP, _VP, _INT, _INT, _I64, _I64, _VP, ctypes.c_size_t, _VP,
                         ctypes.POINTER(_DBL), _VP],
+    "ts_server_create": [ctypes.POINTER(ts_server_cfg), ctypes.POINTER(_VP)],
+    "ts_server_submit": [_VP, ctypes.POINTER(ts_request), ctypes.POINTER(ctypes.c_uint64)],
+    "ts_server_poll": [_VP, ctypes.c_uint64, ctypes.POINTER(ts_result)],
+    "ts_server_wait": [_VP, ctypes.c_uint64, _I64, ctypes.POINTER(ts_result)],
+    "ts_server_fetch": [_VP, ctypes.c_uint64, _VP, _VP, _INT, _INT],
+    "ts_server_release": [_VP, ctypes.c_uint64],
+    "ts_server_cancel": [_VP, ctypes.c_uint64],
+    "ts_server_stats": [_VP, ctypes.POINTER(ts_server_metrics)],
+    "ts_server_destroy": [_VP],
 }
 
 _lock = threading.Lock()
@@ -377,6 +414,80 @@ def adjoint_fidelity_grad(grid, target_re, target_im, steps: int, ckpt_every: in
                         _VP(ws.data_ptr()), nbytes, _VP(grad.data_ptr()), st)
     del keep_t, keep_i
     return F, grad
+
+
+class Server:
+    """The library's continuous-batching request loop (ts_server_*).
+
+    ``submit`` keeps references to the request's input arrays until the
+    request is released, as the C ABI requires them to stay valid."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 64, K: int = 0,
+                 max_epoch_steps: int = 0):
+        cfg = ts_server_cfg(int(hbm_budget_bytes), int(max_slots), int(K), int(max_epoch_steps))
+        self.handle = _VP()
+        _call("ts_server_create", ctypes.byref(cfg), ctypes.byref(self.handle))
+        self._keep = {}
+
+    def submit(self, nx, ny, steps, dt, theta, V, psi_re, psi_im) -> int:
+        """Host numpy / torch arrays or CUDA tensors; V may be None."""
+        shape = (int(ny), int(nx))
+        rp, rdt, rw, k1 = _array_ptr(psi_re, shape)
+        ip, idt, iw, k2 = _array_ptr(psi_im, shape)
+        if (rdt, rw) != (idt, iw):
+            raise ValueError("psi_re and psi_im must share dtype and memory kind")
+        vp, k3 = None, None
+        if V is not None:
+            vp, vdt, vw, k3 = _array_ptr(V, shape)
+            if vdt != TS_F64 or vw != rw:
+                raise ValueError("V must be float64 in the same memory kind as psi")
+        req = ts_request(int(nx), int(ny), int(steps), float(dt), float(theta), vp, rp, ip, rdt, rw)
+        t = ctypes.c_uint64()
+        _call("ts_server_submit", self.handle, ctypes.byref(req), ctypes.byref(t))
+        self._keep[t.value] = (k1, k2, k3)
+        return t.value
+
+    def poll(self, ticket) -> ts_result:
+        r = ts_result()
+        _call("ts_server_poll", self.handle, ticket, ctypes.byref(r))
+        return r
+
+    def wait(self, ticket, timeout_ms: int = -1) -> ts_result:
+        r = ts_result()
+        _call("ts_server_wait", self.handle, ticket, int(timeout_ms), ctypes.byref(r))
+        return r
+
+    def fetch(self, ticket, ny, nx, dtype=np.float64):
+        code = _dtype_code(np.dtype(dtype))
+        re = np.empty((ny, nx), dtype=np.float64 if code == TS_F64 else np.float32)
+        im = np.empty_like(re)
+        _call("ts_server_fetch", self.handle, ticket, _VP(re.ctypes.data), _VP(im.ctypes.data),
+              code, TS_HOST)
+        return re, im
+
+    def release(self, ticket):
+        _call("ts_server_release", self.handle, ticket)
+        self._keep.pop(ticket, None)
+
+    def cancel(self, ticket):
+        _call("ts_server_cancel", self.handle, ticket)
+
+    def stats(self) -> dict:
+        m = ts_server_metrics()
+        _call("ts_server_stats", self.handle, ctypes.byref(m))
+        return {n: getattr(m, n) for n, _ in ts_server_metrics._fields_}
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _call("ts_server_destroy", self.handle)
+        self.handle = None
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def evolve_batched(grids, steps, K: int = 0, stream=None):
