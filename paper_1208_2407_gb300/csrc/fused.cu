@@ -58,8 +58,11 @@ namespace {
 #ifndef TS_FUSED_WPC_DEEP        // ... and for K >= 3
 #define TS_FUSED_WPC_DEEP 1
 #endif
-#ifndef TS_FUSED_PF_SHALLOW      // row pairs prefetched ahead of use for K <= 2
-#define TS_FUSED_PF_SHALLOW 3
+#ifndef TS_FUSED_PF_K1           // row pairs prefetched ahead of use for K = 1
+#define TS_FUSED_PF_K1 4
+#endif
+#ifndef TS_FUSED_PF_K2           // ... for K = 2
+#define TS_FUSED_PF_K2 4
 #endif
 #ifndef TS_FUSED_PF_DEEP         // ... and for K >= 3
 #define TS_FUSED_PF_DEEP 1
@@ -67,10 +70,15 @@ namespace {
 #ifndef TS_FUSED_MIN_BLOCKS      // __launch_bounds__ minimum resident blocks per SM
 #define TS_FUSED_MIN_BLOCKS 1
 #endif
-#ifndef TS_FUSED_UNROLL          // unroll factor of the row-pair loop
-#define TS_FUSED_UNROLL 1
+#ifndef TS_FUSED_PINGPONG_MIN_K  // interior row pairs alternate two carry sets for K in
+#define TS_FUSED_PINGPONG_MIN_K 3    // [MIN_K, MAX_K] (beyond MAX_K the second set spills)
 #endif
-constexpr int ROW_LOOP_UNROLL = TS_FUSED_UNROLL;
+#ifndef TS_FUSED_PINGPONG_MAX_K
+#define TS_FUSED_PINGPONG_MAX_K 6
+#endif
+#ifndef TS_FUSED_ALIGNED         // 1: strip-aligned work split when strips <= warps
+#define TS_FUSED_ALIGNED 1
+#endif
 constexpr int PLANE_SLOT_BYTES = FUSED_BOX_ROWS * FUSED_BOX_COLS * 4;   // 1 KiB
 constexpr int SLOT_BYTES = 2 * PLANE_SLOT_BYTES;     // one ring slot: two planes of 2 rows
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;    // 2 s per wait
@@ -81,12 +89,13 @@ constexpr uint32_t FULL = 0xffffffffu;
 //    pipeline, so it needs PF + 1 slots;
 //  - the phase ring (gamma_V, s_V) is read by the phase of every step, the
 //    last one K row pairs later, so it needs PF + K + 1 slots.
-// Shallow pipelines are memory bound and prefetch deeper; deep ones are
-// arithmetic bound and keep shared memory small for occupancy.
+// Shallow pipelines (K <= 2) are memory bound and prefetch deeper; deep ones
+// are arithmetic bound and keep shared memory small for occupancy.
 template <int K>
 struct Cfg {
     static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
-    static constexpr int PF = K <= 2 ? TS_FUSED_PF_SHALLOW : TS_FUSED_PF_DEEP;
+    static constexpr int PF = K == 1 ? TS_FUSED_PF_K1 : K == 2 ? TS_FUSED_PF_K2 : TS_FUSED_PF_DEEP;
+    static constexpr bool PINGPONG = K >= TS_FUSED_PINGPONG_MIN_K && K <= TS_FUSED_PINGPONG_MAX_K;
     static constexpr int NSS = PF + 1;
     static constexpr int NSP = PF + K + 1;
     static constexpr int HALO = ((2 * K + 3) / 4) * 4;
@@ -106,6 +115,7 @@ struct KParams {
     int n_strips, n_pairs;
     int64_t units;
     int total_warps;
+    int strip_warps;         // > 0: warps per strip of the strip-aligned split
     float t1, s1, g1, t2, s2;
     int *err;
     // adjoint support (K = 1 only): MODE 1 writes the mid-step state m (after
@@ -331,14 +341,17 @@ __device__ __forceinline__ void mid_store(const Frag &m, int row, const Owned &w
 
 __device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
 
-// One row pair through the K-step pipeline.  INTERIOR: every Y pair and
+// One row pair through the K-step pipeline.  The carried rows come in through
+// `cin` and leave through `cout` (each slot is read before it is written, so
+// the two may be the same array).  INTERIOR: every Y pair and
 // every phase row the iteration touches lies on the grid and in the ring,
 // so no masks or range checks are needed.  MODE 0: a plain step; MODE 1
 // (K = 1): also store the mid-step state; MODE 2 (K = 1): a backward step
 // U^dagger (the caller passes the coefficients at -theta; the phase is
 // conjugated here) that accumulates G at its phase point.
 template <int K, bool INTERIOR, int MODE>
-__device__ __forceinline__ void pipeline_step(Frag (&carry)[2 * K], Frag a, Frag b, int yin, int j,
+__device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&cout)[2 * K],
+                                              Frag a, Frag b, int yin, int j,
                                               const unsigned char *ring_p, int pos_p,
                                               const StripCoef &c, const KParams &p, int lane,
                                               const Owned &w, Frag &O0, Frag &O1)
@@ -361,12 +374,12 @@ __device__ __forceinline__ void pipeline_step(Frag (&carry)[2 * K], Frag a, Frag
         const bool v = yok(yin);
         y_pair(a, b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
+    Frag P = cin[0], Q = a;       // rows (yin-1, yin)
     {
         const bool v = yok(yin - 1);
-        y_pair(carry[0], a, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+        y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
-    Frag P = carry[0], Q = a;     // rows (yin-1, yin)
-    carry[0] = b;
+    cout[0] = b;
     int y1 = yin - 1;
     if constexpr (MODE == 2) {
         if (owns_row(w, p, y1)) mid_accumulate(P, y1, w, p);
@@ -401,18 +414,18 @@ __device__ __forceinline__ void pipeline_step(Frag (&carry)[2 * K], Frag a, Frag
         x_even(Q, c.E2);
         x_odd(P, c.O);
         x_odd(Q, c.O);
+        Frag P2 = cin[2 * k - 1], Q2 = P;     // rows (y1-1, y1)
         {   // Ye (2 theta), shifted: pair (y1-1, y1)
             const bool v = yok(y1 - 1);
-            y_pair(carry[2 * k - 1], P, v ? p.t2 : 0.f, v ? p.s2 : 0.f);
+            y_pair(P2, Q2, v ? p.t2 : 0.f, v ? p.s2 : 0.f);
         }
-        Frag P2 = carry[2 * k - 1], Q2 = P;   // rows (y1-1, y1)
-        carry[2 * k - 1] = Q;
+        cout[2 * k - 1] = Q;
+        P = cin[2 * k];                       // rows (y1-2, y1-1)
         {   // Yo (theta), shifted: pair (y1-2, y1-1)
             const bool v = yok(y1 - 2);
-            y_pair(carry[2 * k], P2, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+            y_pair(P, P2, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
         }
-        P = carry[2 * k];                     // rows (y1-2, y1-1)
-        carry[2 * k] = Q2;
+        cout[2 * k] = Q2;
         Q = P2;
         y1 -= 2;
         // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
@@ -430,13 +443,13 @@ __device__ __forceinline__ void pipeline_step(Frag (&carry)[2 * K], Frag a, Frag
         const bool v = yok(y1);
         y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
+    O0 = cin[2 * K - 1];      // rows (y1-1, y1) = (yin-2K, yin-2K+1)
+    O1 = P;
     {
         const bool v = yok(y1 - 1);
-        y_pair(carry[2 * K - 1], P, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+        y_pair(O0, O1, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
-    O0 = carry[2 * K - 1];    // rows (y1-1, y1) = (yin-2K, yin-2K+1)
-    O1 = P;
-    carry[2 * K - 1] = Q;
+    cout[2 * K - 1] = Q;
     x_odd(O0, c.O);
     x_odd(O1, c.O);
     x_even(O0, c.E1);
@@ -481,6 +494,99 @@ __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int wa
 // pipeline: rows [2 q0, 2 q1) are written to (p.out_re, p.out_im).  Returns
 // false if a bounded wait gave up (the error bit is set and this warp's
 // outstanding copies are drained).
+// Per-segment constants of one warp.
+struct Seg {
+    const CUtensorMap *tm_state, *tm_phase;
+    int XL, xg, Y0, Y1, Ys, n_iter, lane;
+    bool store_lane;
+    StripCoef c;
+    Owned own;
+};
+
+template <int K>
+__device__ __forceinline__ void issue_state(WarpRings &r, const Seg &s, int pos, int j)
+{
+    mbar_expect_tx(&r.bar_s[pos], SLOT_BYTES);
+    tma_load_pair(r.ring_s + pos * SLOT_BYTES, s.tm_state, s.XL, s.Ys + 2 * j, &r.bar_s[pos]);
+}
+
+template <int K>
+__device__ __forceinline__ void issue_phase(WarpRings &r, const Seg &s, int pos, int j)
+{
+    mbar_expect_tx(&r.bar_p[pos], SLOT_BYTES);
+    tma_load_pair(r.ring_p + pos * SLOT_BYTES, s.tm_phase, s.XL, s.Ys + 2 * j, &r.bar_p[pos]);
+}
+
+// Row pair j of a segment: wait for its slots, run the pipeline, store the
+// finished rows, refill the freed slots.  Returns false if a bounded wait
+// gave up (after setting the error bit and draining this warp's copies).
+template <int K, int MODE, bool INTERIOR>
+__device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KParams &p, int j,
+                                         const Frag (&cin)[2 * K], Frag (&cout)[2 * K],
+                                         int &issued_s, int &issued_p)
+{
+    using C = Cfg<K>;
+    constexpr int NSS = C::NSS, NSP = C::NSP;
+    const int lane = s.lane;
+    bool ok = mbar_wait(&r.bar_s[r.pos_s], r.par_s, WAIT_LIMIT_NS) &&
+              mbar_wait(&r.bar_p[r.pos_p], r.par_p, WAIT_LIMIT_NS);
+    ok = __all_sync(FULL, ok);
+    if (!ok) {
+        if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
+        // drain this warp's outstanding copies (bounded) before leaving
+        for (int jj = j, ps = r.pos_s, ph = r.par_s; jj < issued_s; ++jj) {
+            mbar_wait(&r.bar_s[ps], ph, WAIT_LIMIT_NS / 4);
+            if (++ps == NSS) { ps = 0; ph ^= 1u; }
+        }
+        for (int jj = j, ps = r.pos_p, ph = r.par_p; jj < issued_p; ++jj) {
+            mbar_wait(&r.bar_p[ps], ph, WAIT_LIMIT_NS / 4);
+            if (++ps == NSP) { ps = 0; ph ^= 1u; }
+        }
+        return false;
+    }
+    const unsigned char *sj = r.ring_s + r.pos_s * SLOT_BYTES;
+    Frag a, b;
+    a.re = lds4(sj, 0, 0, lane);
+    a.im = lds4(sj, 1, 0, lane);
+    b.re = lds4(sj, 0, 1, lane);
+    b.im = lds4(sj, 1, 1, lane);
+    const int yin = s.Ys + 2 * j;
+    Frag O0, O1;
+    pipeline_step<K, INTERIOR, MODE>(cin, cout, a, b, yin, j, r.ring_p, r.pos_p, s.c, p, lane,
+                                     s.own, O0, O1);
+    const int yo = yin - 2 * K;
+    if (s.store_lane && yo >= s.Y0 && yo < s.Y1) {
+        float *rr = p.out_re + (int64_t)yo * p.pitch + s.xg;
+        float *mm = p.out_im + (int64_t)yo * p.pitch + s.xg;
+        if (INTERIOR || yo < p.ny) {
+            *reinterpret_cast<float4 *>(rr) = O0.re;
+            *reinterpret_cast<float4 *>(mm) = O0.im;
+        }
+        if (INTERIOR || yo + 1 < p.ny) {
+            *reinterpret_cast<float4 *>(rr + p.pitch) = O1.re;
+            *reinterpret_cast<float4 *>(mm + p.pitch) = O1.im;
+        }
+    }
+    // state slot j and phase slot j-K are no longer read: refill them with
+    // row pairs j + NSS and j - K + NSP (the same ring positions)
+    __syncwarp();
+    const int js = j + NSS, jp = j - K + NSP;
+    const bool more_s = js < s.n_iter, more_p = j >= K && jp < s.n_iter;
+    if (lane == 0 && (more_s || more_p)) {
+        fence_proxy_async();
+        if (more_s) issue_state<K>(r, s, r.pos_s, js);
+        if (more_p) issue_phase<K>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
+    }
+    issued_s += more_s;
+    issued_p += more_p;
+    if (++r.pos_s == NSS) { r.pos_s = 0; r.par_s ^= 1u; }
+    if (++r.pos_p == NSP) { r.pos_p = 0; r.par_p ^= 1u; }
+    return true;
+}
+
+// Stream the row pairs [q0, q1) of strip sx of one grid through the K-step
+// pipeline: rows [2 q0, 2 q1) are written to (p.out_re, p.out_im).  Returns
+// false if a bounded wait gave up.
 template <int K, int MODE>
 __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_state,
                                             const CUtensorMap *tm_phase, const KParams &p,
@@ -488,110 +594,67 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
 {
     using C = Cfg<K>;
     constexpr int NSS = C::NSS, NSP = C::NSP, HALO = C::HALO, VALID = C::VALID;
-    const int XL = sx * VALID - HALO;              // first loaded column (multiple of 4)
-    const int xg = XL + 4 * lane;                  // this lane's first column
-    const int Y0 = 2 * q0, Y1 = 2 * q1;            // output rows [Y0, Y1)
-    const int Ys = Y0 - 2 * K;                     // first loaded row
-    const int n_iter = (Y1 - Y0) / 2 + 2 * K;      // row pairs loaded
+    Seg s;
+    s.tm_state = tm_state;
+    s.tm_phase = tm_phase;
+    s.lane = lane;
+    s.XL = sx * VALID - HALO;            // first loaded column (multiple of 4)
+    s.xg = s.XL + 4 * lane;              // this lane's first column
+    s.Y0 = 2 * q0;                       // output rows [Y0, Y1)
+    s.Y1 = 2 * q1;
+    s.Ys = s.Y0 - 2 * K;                 // first loaded row
+    s.n_iter = (s.Y1 - s.Y0) / 2 + 2 * K;   // row pairs loaded
 
     // pair (x, x+1) is rotated iff both sites are on the grid
+    const int xg = s.xg;
     auto xok = [&](int x) { return x >= 0 && x + 1 < p.nx; };
     const bool e0 = xok(xg), e1 = xok(xg + 2), o0 = xok(xg + 1), oR = xok(xg + 3),
                oL = xok(xg - 1);
-    StripCoef c;
-    c.E1 = {e0 ? p.t1 : 0.f, e0 ? p.s1 : 0.f, e1 ? p.t1 : 0.f, e1 ? p.s1 : 0.f};
-    c.E2 = {e0 ? p.t2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.t2 : 0.f, e1 ? p.s2 : 0.f};
-    c.O = {o0 ? p.t1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
-           oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
-    const bool store_lane = lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
-    const Owned own = {Y0, Y1, xg, store_lane};
+    s.c.E1 = {e0 ? p.t1 : 0.f, e0 ? p.s1 : 0.f, e1 ? p.t1 : 0.f, e1 ? p.s1 : 0.f};
+    s.c.E2 = {e0 ? p.t2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.t2 : 0.f, e1 ? p.s2 : 0.f};
+    s.c.O = {o0 ? p.t1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
+             oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
+    s.store_lane = lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
+    s.own = {s.Y0, s.Y1, xg, s.store_lane};
 
-    // lane 0 only: fill ring position `pos` with row pair j
-    auto issue_state = [&](int pos, int j) {
-        mbar_expect_tx(&r.bar_s[pos], SLOT_BYTES);
-        tma_load_pair(r.ring_s + pos * SLOT_BYTES, tm_state, XL, Ys + 2 * j, &r.bar_s[pos]);
-    };
-    auto issue_phase = [&](int pos, int j) {
-        mbar_expect_tx(&r.bar_p[pos], SLOT_BYTES);
-        tma_load_pair(r.ring_p + pos * SLOT_BYTES, tm_phase, XL, Ys + 2 * j, &r.bar_p[pos]);
-    };
-    const int n_pro_s = n_iter < NSS ? n_iter : NSS;
-    const int n_pro_p = n_iter < NSP ? n_iter : NSP;
+    const int n_pro_s = s.n_iter < NSS ? s.n_iter : NSS;
+    const int n_pro_p = s.n_iter < NSP ? s.n_iter : NSP;
     if (lane == 0) {
         fence_proxy_async();
         for (int j = 0; j < n_pro_p; ++j) {
-            if (j < n_pro_s) issue_state((r.pos_s + j) % NSS, j);
-            issue_phase((r.pos_p + j) % NSP, j);
+            if (j < n_pro_s) issue_state<K>(r, s, (r.pos_s + j) % NSS, j);
+            issue_phase<K>(r, s, (r.pos_p + j) % NSP, j);
         }
     }
     int issued_s = n_pro_s, issued_p = n_pro_p;
 
-    Frag carry[2 * K];
+    // Carried rows: interior row pairs go in twos; for deep pipelines the
+    // first reads set A and writes set B and the second goes back into A, so
+    // no row is copied between iterations (at the price of registers, which
+    // shallow pipelines keep for occupancy); edge row pairs update A in place.
+    Frag cA[2 * K], cB[2 * K];
 #pragma unroll
-    for (int i = 0; i < 2 * K; ++i) carry[i] = zero_frag();
-
-#pragma unroll ROW_LOOP_UNROLL
-    for (int j = 0; j < n_iter; ++j) {
-        bool ok = mbar_wait(&r.bar_s[r.pos_s], r.par_s, WAIT_LIMIT_NS) &&
-                  mbar_wait(&r.bar_p[r.pos_p], r.par_p, WAIT_LIMIT_NS);
-        ok = __all_sync(FULL, ok);
-        if (!ok) {
-            if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
-            // drain this warp's outstanding copies (bounded) before leaving
-            for (int jj = j, ps = r.pos_s, ph = r.par_s; jj < issued_s; ++jj) {
-                mbar_wait(&r.bar_s[ps], ph, WAIT_LIMIT_NS / 4);
-                if (++ps == NSS) { ps = 0; ph ^= 1u; }
+    for (int i = 0; i < 2 * K; ++i) cA[i] = zero_frag();
+    auto interior = [&](int j) {
+        const int yin = s.Ys + 2 * j;
+        return j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny;
+    };
+    for (int j = 0; j < s.n_iter;) {
+        if (j + 1 < s.n_iter && interior(j) && interior(j + 1)) {
+            if (C::PINGPONG) {
+                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cB, issued_s, issued_p)) return false;
+                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cB, cA, issued_s, issued_p))
+                    return false;
+            } else {
+                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cA, issued_s, issued_p)) return false;
+                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cA, cA, issued_s, issued_p))
+                    return false;
             }
-            for (int jj = j, ps = r.pos_p, ph = r.par_p; jj < issued_p; ++jj) {
-                mbar_wait(&r.bar_p[ps], ph, WAIT_LIMIT_NS / 4);
-                if (++ps == NSP) { ps = 0; ph ^= 1u; }
-            }
-            return false;
+            j += 2;
+        } else {
+            if (!row_pair<K, MODE, false>(r, s, p, j, cA, cA, issued_s, issued_p)) return false;
+            j += 1;
         }
-        const unsigned char *sj = r.ring_s + r.pos_s * SLOT_BYTES;
-        Frag a, b;
-        a.re = lds4(sj, 0, 0, lane);
-        a.im = lds4(sj, 1, 0, lane);
-        b.re = lds4(sj, 0, 1, lane);
-        b.im = lds4(sj, 1, 1, lane);
-        const int yin = Ys + 2 * j;
-        Frag O0, O1;
-        const bool interior = j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny;
-        if (interior)
-            pipeline_step<K, true, MODE>(carry, a, b, yin, j, r.ring_p, r.pos_p, c, p, lane, own,
-                                         O0, O1);
-        else
-            pipeline_step<K, false, MODE>(carry, a, b, yin, j, r.ring_p, r.pos_p, c, p, lane, own,
-                                          O0, O1);
-
-        const int yo = yin - 2 * K;
-        if (store_lane && yo >= Y0 && yo < Y1) {
-            float *rr = p.out_re + (int64_t)yo * p.pitch + xg;
-            float *mm = p.out_im + (int64_t)yo * p.pitch + xg;
-            if (yo < p.ny) {
-                *reinterpret_cast<float4 *>(rr) = O0.re;
-                *reinterpret_cast<float4 *>(mm) = O0.im;
-            }
-            if (yo + 1 < p.ny) {
-                *reinterpret_cast<float4 *>(rr + p.pitch) = O1.re;
-                *reinterpret_cast<float4 *>(mm + p.pitch) = O1.im;
-            }
-        }
-
-        // state slot j and phase slot j-K are no longer read: refill them
-        // with row pairs j + NSS and j - K + NSP (the same ring positions)
-        __syncwarp();
-        const int js = j + NSS, jp = j - K + NSP;
-        const bool more_s = js < n_iter, more_p = j >= K && jp < n_iter;
-        if (lane == 0 && (more_s || more_p)) {
-            fence_proxy_async();
-            if (more_s) issue_state(r.pos_s, js);
-            if (more_p) issue_phase(r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
-        }
-        issued_s += more_s;
-        issued_p += more_p;
-        if (++r.pos_s == NSS) { r.pos_s = 0; r.par_s ^= 1u; }
-        if (++r.pos_p == NSP) { r.pos_p = 0; r.par_p ^= 1u; }
     }
     __syncwarp();
     return true;
@@ -609,6 +672,16 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
     const int gw = blockIdx.x * Cfg<K>::WPC + warp;
     if (gw >= p.total_warps) return;
     WarpRings r = carve_rings<K>(smem_raw, warp, lane);
+    if (p.strip_warps > 0) {
+        // strip-aligned split: warp (sx, i) takes row range i of strip sx, so
+        // warps of neighbouring strips walk the same rows at the same time and
+        // the columns their halos share are read from L2
+        const int sx = gw / p.strip_warps, i = gw - sx * p.strip_warps;
+        const int q0 = (int)((int64_t)i * p.n_pairs / p.strip_warps);
+        const int q1 = (int)((int64_t)(i + 1) * p.n_pairs / p.strip_warps);
+        if (q1 > q0) run_segment<K, MODE>(r, &tm_state, &tm_phase, p, sx, q0, q1, lane);
+        return;
+    }
     const int64_t u_begin = (int64_t)gw * p.units / p.total_warps;
     const int64_t u_end = (int64_t)(gw + 1) * p.units / p.total_warps;
     for (int64_t u = u_begin; u < u_end;) {
@@ -665,6 +738,7 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
         p.s2 = d->s2;
         p.err = err;
         p.n_pairs = (p.ny + 1) / 2;
+        p.strip_warps = 0;
         const int64_t local = u - e.unit_begin;
         const int64_t g_units = (gi + 1 < n_grids ? tab[gi + 1].unit_begin : total_units) -
                                 e.unit_begin;
@@ -710,6 +784,15 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     int64_t want = (p.units + 15) / 16;
     int64_t cap = (int64_t)num_sms * blocks_per_sm * C::WPC;
     p.total_warps = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+    p.strip_warps = 0;
+    if (TS_FUSED_ALIGNED && p.n_strips <= cap) {
+        int64_t w = cap / p.n_strips;
+        const int64_t rows_cap = (p.n_pairs + 15) / 16;
+        if (w > rows_cap) w = rows_cap;
+        if (w < 1) w = 1;
+        p.strip_warps = (int)w;
+        p.total_warps = (int)(w * p.n_strips);
+    }
     p.t1 = a.t1;
     p.s1 = a.s1;
     p.g1 = a.g1;
