@@ -217,6 +217,36 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# DRAM traffic of the fused kernel from the committed ncu record
+# ---------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("fused.cu", "common.cuh", "ffloat.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1208_2407_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(n: int, K: int):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of
+    fused_kernel<K> on an n x n grid, from profiles/fused_kernel_traffic.json,
+    or None if there is no record for this case or the kernel source changed
+    since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    for e in rec.get("captures", []):
+        if e.get("n") == n and e.get("K") == K:
+            return e.get("dram_bytes_per_launch")
+    return None
+
+
+# ---------------------------------------------------------------------------
 # serving: Poisson arrivals of mixed grids, continuous batching vs one at a time
 # ---------------------------------------------------------------------------
 def serve_bench(n_requests: int, seed: int, budget_gb: float = 120.0):
@@ -408,8 +438,9 @@ def run_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved_gbs = BYTES_PER_SITE_LAUNCH * float(n) * n / (avg_launch_ms / 1e3) / 1e9
+    traffic = recorded_traffic(n, k_eff)
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic, "peak_source": peak_src,
                 "kernel": "fused_kernel<%d>" % k_eff,
                 "avg_launch_ms": avg_launch_ms,
                 "algorithmic_bytes_per_launch": BYTES_PER_SITE_LAUNCH * n * n}
