@@ -368,7 +368,7 @@ def run_ours(args):
     el_ms = start.elapsed_time(end)
     el_ms = dist.max(el_ms)
     evolve_ms = sum(a.elapsed_time(b) for a, b in ev_pairs)
-    k_eff = K if K > 0 else 4
+    k_eff = K if K > 0 else trotter.ts_fused_default_depth()
     fused_launches_per_step = (T + k_eff - 1) // k_eff
     avg_launch_ms = evolve_ms / (fused_launches_per_step * args.steps)
 

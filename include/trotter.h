@@ -277,6 +277,9 @@ ts_status ts_norm_noalloc(const void *re, const void *im, ts_dtype dtype, int64_
                           int64_t ny, int64_t pitch, double *out, void *stream);
 size_t ts_norm_noalloc_scratch_bytes(void);
 
+/* The fused depth ts_evolve uses when K = 0. */
+int ts_fused_default_depth(void);
+
 /* Number of kernels this thread's calls enqueued since the last reset. */
 int64_t ts_launch_count(int reset);
 

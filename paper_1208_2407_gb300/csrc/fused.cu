@@ -70,6 +70,9 @@ namespace {
 #ifndef TS_FUSED_MIN_BLOCKS      // __launch_bounds__ minimum resident blocks per SM
 #define TS_FUSED_MIN_BLOCKS 1
 #endif
+#ifndef TS_FUSED_MIN_BLOCKS_K3   // ... for K = 3: 168 registers, 12 one-warp blocks per SM
+#define TS_FUSED_MIN_BLOCKS_K3 9
+#endif
 #ifndef TS_FUSED_PINGPONG_MIN_K  // interior row pairs alternate two carry sets for K in
 #define TS_FUSED_PINGPONG_MIN_K 3    // [MIN_K, MAX_K] (beyond MAX_K the second set spills)
 #endif
@@ -96,6 +99,7 @@ struct Cfg {
     static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
     static constexpr int PF = K == 1 ? TS_FUSED_PF_K1 : K == 2 ? TS_FUSED_PF_K2 : TS_FUSED_PF_DEEP;
     static constexpr bool PINGPONG = K >= TS_FUSED_PINGPONG_MIN_K && K <= TS_FUSED_PINGPONG_MAX_K;
+    static constexpr int MINB = K == 3 ? TS_FUSED_MIN_BLOCKS_K3 : TS_FUSED_MIN_BLOCKS;
     static constexpr int NSS = PF + 1;
     static constexpr int NSP = PF + K + 1;
     static constexpr int HALO = ((2 * K + 3) / 4) * 4;
@@ -663,7 +667,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
 // One grid; the (strip, row-pair) units are split into equal contiguous
 // ranges, one per warp of a persistent launch.
 template <int K, int MODE>
-__global__ void __launch_bounds__(Cfg<K>::WPC * 32, TS_FUSED_MIN_BLOCKS)
+__global__ void __launch_bounds__(Cfg<K>::WPC * 32, Cfg<K>::MINB)
 fused_kernel(const __grid_constant__ CUtensorMap tm_state,
              const __grid_constant__ CUtensorMap tm_phase, const KParams p)
 {

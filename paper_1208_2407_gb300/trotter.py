@@ -133,6 +133,8 @@ def load():
         lib.ts_last_error.restype = ctypes.c_char_p
         lib.ts_launch_count.argtypes = [_INT]
         lib.ts_launch_count.restype = _I64
+        lib.ts_fused_default_depth.argtypes = []
+        lib.ts_fused_default_depth.restype = _INT
         lib.ts_norm_noalloc_scratch_bytes.argtypes = []
         lib.ts_norm_noalloc_scratch_bytes.restype = ctypes.c_size_t
         _lib = lib
@@ -142,7 +144,8 @@ def load():
 def exported_symbols():
     """Names the header declares, for the ABI test."""
     return sorted(list(_SIGNATURES) + ["ts_last_error", "ts_launch_count",
-                                        "ts_norm_noalloc_scratch_bytes"])
+                                        "ts_norm_noalloc_scratch_bytes",
+                                        "ts_fused_default_depth"])
 
 
 def _check(status: int):
@@ -257,6 +260,10 @@ def ts_norm_noalloc(re_ptr, im_ptr, dtype, nx, ny, pitch, out_ptr, stream):
 
 def ts_norm_noalloc_scratch_bytes() -> int:
     return int(load().ts_norm_noalloc_scratch_bytes())
+
+
+def ts_fused_default_depth() -> int:
+    return int(load().ts_fused_default_depth())
 
 
 def ts_launch_count(reset: bool = False) -> int:

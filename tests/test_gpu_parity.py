@@ -264,6 +264,12 @@ def test_argument_errors_and_launch_count():
         trotter.ts_launch_count(reset=True)
         g.evolve(10, K=4)           # 4 + 4 + 2
         assert trotter.ts_launch_count() == 3
+        trotter.ts_launch_count(reset=True)
+        g.evolve(10)                # the default depth
+        d = trotter.ts_fused_default_depth()
+        assert 1 <= d <= 8 and trotter.ts_launch_count() == (10 + d - 1) // d
+        trotter.ts_launch_count(reset=True)
+        g.evolve(10, K=4)
         g.evolve_plain(2)
         assert trotter.ts_launch_count() == 3 + 18
     finally:
