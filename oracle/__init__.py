@@ -42,40 +42,43 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def bind(lib):
+    """Declare the C signatures on a loaded oracle library (the built one or,
+    in the planted-mistake tests, a mutant compiled from edited source)."""
+    sig = {
+        "oracle_sweep_x": [_I64, _I64, _DP, _DP, ctypes.c_int, ctypes.c_double, ctypes.c_int],
+        "oracle_sweep_y": [_I64, _I64, _DP, _DP, ctypes.c_int, ctypes.c_double, ctypes.c_int],
+        "oracle_phase": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, ctypes.c_int],
+        "oracle_step2": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double, ctypes.c_int],
+        "oracle_evolve": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double, _I64,
+                          ctypes.c_int, ctypes.c_int],
+        "oracle_moments": [_I64, _I64, _DP, _DP, _DP],
+        "oracle_energy": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, _DP],
+        "oracle_inner": [_I64, _DP, _DP, _DP, _DP, _DP],
+        "oracle_adjoint_grad": [_I64, _I64, _DP, _DP, _DP, _DP, _DP, ctypes.c_double,
+                                ctypes.c_double, _I64, _DP, _DP, _DP, ctypes.c_int],
+        "oracle_apply_A": [_I64, _I64, _DP, _DP, ctypes.c_double, ctypes.c_int],
+        "oracle_apply_B": [_I64, _I64, _DP, _DP, ctypes.c_double, ctypes.c_int],
+        "oracle_compensated_sum": [_I64, _DP],
+    }
+    for name, args in sig.items():
+        getattr(lib, name).argtypes = args
+    for name in ("oracle_evolve", "oracle_adjoint_grad"):
+        getattr(lib, name).restype = ctypes.c_int
+    for name in ("oracle_sweep_x", "oracle_sweep_y", "oracle_phase", "oracle_step2",
+                 "oracle_moments", "oracle_energy", "oracle_inner", "oracle_apply_A",
+                 "oracle_apply_B"):
+        getattr(lib, name).restype = None
+    lib.oracle_compensated_sum.restype = ctypes.c_double
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        sig = {
-            "oracle_sweep_x": [_I64, _I64, _DP, _DP, ctypes.c_int, ctypes.c_double, ctypes.c_int],
-            "oracle_sweep_y": [_I64, _I64, _DP, _DP, ctypes.c_int, ctypes.c_double, ctypes.c_int],
-            "oracle_phase": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, ctypes.c_int],
-            "oracle_step2": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double, ctypes.c_int],
-            "oracle_evolve": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double, _I64,
-                              ctypes.c_int, ctypes.c_int],
-            "oracle_moments": [_I64, _I64, _DP, _DP, _DP],
-            "oracle_energy": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, _DP],
-            "oracle_inner": [_I64, _DP, _DP, _DP, _DP, _DP],
-            "oracle_adjoint_grad": [_I64, _I64, _DP, _DP, _DP, _DP, _DP, ctypes.c_double,
-                                    ctypes.c_double, _I64, _DP, _DP, _DP, ctypes.c_int],
-            "oracle_apply_A": [_I64, _I64, _DP, _DP, ctypes.c_double, ctypes.c_int],
-            "oracle_apply_B": [_I64, _I64, _DP, _DP, ctypes.c_double, ctypes.c_int],
-            "oracle_compensated_sum": [_I64, _DP],
-        }
-        for name, args in sig.items():
-            fn = getattr(lib, name)
-            fn.argtypes = args
-        for name in ("oracle_evolve", "oracle_adjoint_grad"):
-            getattr(lib, name).restype = ctypes.c_int
-        for name in ("oracle_sweep_x", "oracle_sweep_y", "oracle_phase", "oracle_step2",
-                     "oracle_moments", "oracle_energy", "oracle_inner", "oracle_apply_A",
-                     "oracle_apply_B"):
-            getattr(lib, name).restype = None
-        lib.oracle_compensated_sum.restype = ctypes.c_double
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = bind(ctypes.CDLL(build()))
+        return _lib
 
 
 def _f64(a):
