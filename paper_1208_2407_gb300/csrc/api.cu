@@ -76,6 +76,9 @@ ts_status grid_setup(const ts_layout &L, void *slab, bool owns_slab, ts_grid **o
     g->cur = 0;
     g->dt = g->theta = g->J = 0.0;
     g->g1 = g->s1 = g->t1 = g->s2 = g->t2 = 0.0;
+    g->order = 2;
+    g->sub[0] = g->sub[1] = RotCoef{0.0, 0.0, 0.0, 0.0, 0.0};
+    g->tab_b = nullptr;
     g->tmaps_ok = false;
     if (L.dtype == TS_F32) {
         const char *why = "";
@@ -97,20 +100,26 @@ ts_status grid_setup(const ts_layout &L, void *slab, bool owns_slab, ts_grid **o
 
 size_t grid_scratch_offset(const ts_layout &L) { return kPlanes * L.plane_bytes; }
 
+RotCoef rot_coef(double theta)
+{
+    // versine form (g = 1 - cos theta = 2 sin^2(theta/2), s = sin theta) and
+    // lifting form (t = tan(theta/2), s); the merged angle 2 theta in lifting form
+    const double sh1 = std::sin(0.5 * theta);
+    return RotCoef{2.0 * sh1 * sh1, std::sin(theta), std::tan(0.5 * theta),
+                   std::sin(2.0 * theta), std::tan(theta)};
+}
+
 void grid_set_coefficients(ts_grid *g, double dt, double theta, cudaStream_t st)
 {
     g->dt = dt;
     g->theta = theta;
     g->J = dt != 0.0 ? 2.0 * theta / dt : 0.0;
-    // kinetic rotation coefficients in FP64, rounded once where used:
-    // versine form (g = 1 - cos theta = 2 sin^2(theta/2), s = sin theta) and
-    // lifting form (t = tan(theta/2), s); the merged angle 2 theta in lifting form
-    const double sh1 = std::sin(0.5 * theta);
-    g->g1 = 2.0 * sh1 * sh1;
-    g->s1 = std::sin(theta);
-    g->t1 = std::tan(0.5 * theta);
-    g->s2 = std::sin(2.0 * theta);
-    g->t2 = std::tan(theta);
+    const RotCoef c = rot_coef(theta);
+    g->g1 = c.g1;
+    g->s1 = c.s1;
+    g->t1 = c.t1;
+    g->s2 = c.s2;
+    g->t2 = c.t2;
     if (!g->f64()) grid_write_desc(g, st);
 }
 
@@ -282,6 +291,10 @@ ts_status ts_destroy_grid(ts_grid *g)
     ts::forget_adjoint(g);
     cudaError_t e = cudaSuccess;
     if (g->owns_slab) e = cudaFree(g->slab);
+    if (g->tab_b) {
+        cudaError_t f = cudaFree(g->tab_b);
+        if (e == cudaSuccess) e = f;
+    }
     delete g;
     if (e != cudaSuccess) return cuda_fail(e, "ts_destroy_grid: cudaFree");
     return TS_OK;
@@ -424,17 +437,49 @@ ts_status ts_get_state(ts_grid *g, void *re, void *im, ts_dtype dst_dtype, ts_me
 ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt, double theta,
                            void *stream)
 {
+    return ts_set_potential_order(g, V, where, dt, theta, 2, stream);
+}
+
+ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, double dt,
+                                 double theta, int order, void *stream)
+{
     if (!g) return fail(TS_ERR_ARG, "ts_set_potential: grid is NULL");
     if (!std::isfinite(dt) || !std::isfinite(theta))
         return fail(TS_ERR_ARG, "ts_set_potential: dt and theta must be finite");
     if (where != TS_HOST && where != TS_DEVICE)
         return fail(TS_ERR_ARG, "ts_set_potential: unknown memory kind");
+    if (order != 2 && order != 4)
+        return fail(TS_ERR_ARG, "ts_set_potential_order: order must be 2 or 4, got %d", order);
     cudaStream_t st = (cudaStream_t)stream;
-    ts::grid_set_coefficients(g, dt, theta, st);
     const int nx = (int)g->L.nx, ny = (int)g->L.ny;
     cudaError_t e;
+    // fourth order (Eq. fourthorder): U4(dt) = U2(p dt)^2 U2((1-4p) dt) U2(p dt)^2
+    // with p = 1 / (4 - 4^(1/3)); substep a = p dt uses planes 4/5, substep
+    // b = (1 - 4p) dt a second table allocated here on first use
+    const double p4 = 1.0 / (4.0 - std::cbrt(4.0));
+    const double w[2] = {p4, 1.0 - 4.0 * p4};
+    if (order == 4 && !g->tab_b) {
+        unsigned char *tb = nullptr;
+        e = cudaMalloc((void **)&tb, 2 * g->L.plane_bytes);
+        if (e != cudaSuccess) return fail(TS_ERR_OOM, "ts_set_potential_order: second table: %s",
+                                          cudaGetErrorString(e));
+        if (!g->f64()) {
+            const char *why = "";
+            if (!ts::make_pair_tensor_map(&g->tm_phase_b, tb, nx, ny, g->L.pitch,
+                                          g->L.plane_bytes, &why)) {
+                cudaFree(tb);
+                return fail(TS_ERR_CUDA, "ts_set_potential_order: %s", why);
+            }
+        }
+        g->tab_b = tb;
+    }
+    ts::grid_set_coefficients(g, dt, theta, st);
+    g->order = order;
+    if (order == 4)
+        for (int i = 0; i < 2; ++i) g->sub[i] = ts::rot_coef(w[i] * theta);
     if (!V) {
         e = cudaMemsetAsync(g->pg(), 0, 3 * g->L.plane_bytes, st);   // planes 4, 5, 6
+        if (e == cudaSuccess && order == 4) e = cudaMemsetAsync(g->tab_b, 0, 2 * g->L.plane_bytes, st);
         if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: clear");
         return TS_OK;
     }
@@ -445,8 +490,11 @@ ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
         if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: host-to-device copy");
         src = (const double *)g->re_other();
     }
-    e = ts::launch_phase_table(src, g->pg(), g->ps(), g->vp(), g->f64(), nx, ny, g->L.pitch, dt,
-                               st);
+    e = ts::launch_phase_table(src, g->pg(), g->ps(), g->vp(), g->f64(), nx, ny, g->L.pitch,
+                               order == 4 ? w[0] * dt : dt, st);
+    if (e == cudaSuccess && order == 4)
+        e = ts::launch_phase_table(src, g->pg_b(), g->ps_b(), g->vp(), g->f64(), nx, ny,
+                                   g->L.pitch, w[1] * dt, st);
     if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: table kernel");
     if (where == TS_HOST) {
         e = cudaStreamSynchronize(st);
@@ -457,13 +505,16 @@ ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
 
 namespace {
 
-ts_status plain_steps(ts_grid *g, int64_t steps, cudaStream_t st)
+// `steps` second-order steps, one kernel per sweep, with the rotation
+// coefficients c and the phase table (pg, ps).
+ts_status plain_run(ts_grid *g, int64_t steps, const ts::RotCoef &c, const void *pg,
+                    const void *ps, cudaStream_t st)
 {
     const int nx = (int)g->L.nx, ny = (int)g->L.ny;
     const int64_t pitch = g->L.pitch;
     void *re = g->re(), *im = g->im();
     const bool f = g->f64();
-    double gg = g->g1, ss = g->s1;
+    double gg = c.g1, ss = c.s1;
     if (!f) {   // FP32 path: coefficients rounded once to float
         gg = (double)(float)gg;
         ss = (double)(float)ss;
@@ -474,7 +525,7 @@ ts_status plain_steps(ts_grid *g, int64_t steps, cudaStream_t st)
         for (int i = 0; i < 4 && e == cudaSuccess; ++i)
             e = ts::launch_plain_sweep(re, im, f, nx, ny, pitch, seq_axis[i], seq_par[i], gg, ss, st);
         if (e == cudaSuccess)
-            e = ts::launch_plain_phase(re, im, g->pg(), g->ps(), f, nx, ny, pitch, st);
+            e = ts::launch_plain_phase(re, im, pg, ps, f, nx, ny, pitch, st);
         for (int i = 3; i >= 0 && e == cudaSuccess; --i)
             e = ts::launch_plain_sweep(re, im, f, nx, ny, pitch, seq_axis[i], seq_par[i], gg, ss, st);
         if (e != cudaSuccess) return cuda_fail(e, "plain sweep launch");
@@ -484,7 +535,10 @@ ts_status plain_steps(ts_grid *g, int64_t steps, cudaStream_t st)
 
 
 
-ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
+// `steps` second-order steps on the fused path at depth K (a remainder runs
+// at a smaller depth), with the coefficients c and the phase table map tm.
+ts_status fused_run(ts_grid *g, int64_t steps, int K, const ts::RotCoef &c,
+                    const CUtensorMap *tm, cudaStream_t st)
 {
     if (!g->tmaps_ok) return fail(TS_ERR_STATE, "fused path: tensor maps missing");
     int64_t left = steps;
@@ -492,17 +546,17 @@ ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
         const int k = (int)(left >= K ? K : left);
         ts::FusedLaunch a;
         a.tm_state = &g->tm_state[g->cur];
-        a.tm_phase = &g->tm_phase;
+        a.tm_phase = tm;
         a.out_re = (float *)g->re_other();
         a.out_im = (float *)g->im_other();
         a.nx = (int)g->L.nx;
         a.ny = (int)g->L.ny;
         a.pitch = g->L.pitch;
-        a.t1 = (float)g->t1;
-        a.s1 = (float)g->s1;
-        a.g1 = (float)g->g1;
-        a.t2 = (float)g->t2;
-        a.s2 = (float)g->s2;
+        a.t1 = (float)c.t1;
+        a.s1 = (float)c.s1;
+        a.g1 = (float)c.g1;
+        a.t2 = (float)c.t2;
+        a.s2 = (float)c.s2;
         a.err = g->err;
         cudaError_t e = ts::launch_fused(k, a, st);
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
@@ -510,6 +564,48 @@ ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
         left -= k;
     }
     return TS_OK;
+}
+
+ts::RotCoef grid_coef(const ts_grid *g) { return ts::RotCoef{g->g1, g->s1, g->t1, g->s2, g->t2}; }
+
+ts_status plain_steps(ts_grid *g, int64_t steps, cudaStream_t st)
+{
+    return plain_run(g, steps, grid_coef(g), g->pg(), g->ps(), st);
+}
+
+ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
+{
+    return fused_run(g, steps, K, grid_coef(g), &g->tm_phase, st);
+}
+
+// Fourth-order steps (Eq. fourthorder): the substeps a = U2(p dt) and
+// b = U2((1-4p) dt) in the order a a b a a per step.  The a substeps of
+// neighbouring steps run back to back (a run of 2 at either end, of 4
+// between two b substeps), so on the fused path each run of r substeps is
+// ceil(r / K) launches of near-equal depth; each b substep is one launch.
+ts_status evolve4(ts_grid *g, int64_t steps, int K, bool plain, cudaStream_t st)
+{
+    const int depth = K == 0 ? 4 : K;
+    auto run_a = [&](int64_t r) -> ts_status {
+        if (plain) return plain_run(g, r, g->sub[0], g->pg(), g->ps(), st);
+        const int64_t n = (r + depth - 1) / depth;
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t k = r / n + (i < r % n ? 1 : 0);
+            ts_status s = fused_run(g, k, (int)k, g->sub[0], &g->tm_phase, st);
+            if (s != TS_OK) return s;
+        }
+        return TS_OK;
+    };
+    auto run_b = [&]() -> ts_status {
+        if (plain) return plain_run(g, 1, g->sub[1], g->pg_b(), g->ps_b(), st);
+        return fused_run(g, 1, 1, g->sub[1], &g->tm_phase_b, st);
+    };
+    ts_status s = run_a(2);
+    for (int64_t n = 0; n < steps && s == TS_OK; ++n) {
+        s = run_b();
+        if (s == TS_OK) s = run_a(n + 1 < steps ? 4 : 2);
+    }
+    return s;
 }
 
 }  // namespace
@@ -521,11 +617,15 @@ ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
     if (K < 0 || K > ts::FUSED_MAX_K) return fail(TS_ERR_ARG, "ts_evolve: K must be in [0, 8]");
     if (steps == 0) return TS_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    if (g->f64()) {
-        if (K != 0)
-            return fail(TS_ERR_UNSUPPORTED, "ts_evolve: FP64 grids run the plain path (K must be 0)");
-        return plain_steps(g, steps, st);
+    if (g->f64() && K != 0)
+        return fail(TS_ERR_UNSUPPORTED, "ts_evolve: FP64 grids run the plain path (K must be 0)");
+    if (g->order == 4) {
+        // the substep angles p theta and (1-4p) theta must both suit the fused kernel
+        const double p4 = 1.0 / (4.0 - std::cbrt(4.0));
+        const bool plain = g->f64() || std::fabs(g->theta) * std::fabs(1.0 - 4.0 * p4) > 0.25 * M_PI;
+        return evolve4(g, steps, K, plain, st);
     }
+    if (g->f64()) return plain_steps(g, steps, st);
     // The fused kernel applies the rotations at theta and 2 theta as three
     // shears with tan(theta/2) and tan(theta); it requires |theta| <= pi/4
     // (|2 theta| <= pi/2).  Larger angles -- far beyond any useful Trotter
@@ -538,6 +638,8 @@ ts_status ts_evolve_plain(ts_grid *g, int64_t steps, void *stream)
 {
     if (!g) return fail(TS_ERR_ARG, "ts_evolve_plain: grid is NULL");
     if (steps < 0) return fail(TS_ERR_ARG, "ts_evolve_plain: negative step count");
+    if (steps == 0) return TS_OK;
+    if (g->order == 4) return evolve4(g, steps, 0, true, (cudaStream_t)stream);
     return plain_steps(g, steps, (cudaStream_t)stream);
 }
 
@@ -547,14 +649,14 @@ ts_status ts_evolve_batched(ts_grid *const *gs, int n, const int64_t *steps, int
     if (K < 0 || K > ts::FUSED_MAX_K) return fail(TS_ERR_ARG, "ts_evolve_batched: K must be in [0, 8]");
     cudaStream_t st = (cudaStream_t)stream;
     const int depth = K == 0 ? auto_depth() : K;
-    // grids the multi-grid kernel can take: FP32, |theta| <= pi/4; the rest
-    // evolve one by one
+    // grids the multi-grid kernel can take: FP32, second order, |theta| <=
+    // pi/4; the rest evolve one by one
     std::vector<ts_grid *> multi;
     std::vector<int64_t> msteps;
     for (int i = 0; i < n; ++i) {
         if (!gs[i] || steps[i] < 0) return fail(TS_ERR_ARG, "ts_evolve_batched: grid %d", i);
         if (steps[i] == 0) continue;
-        if (gs[i]->f64() || std::fabs(gs[i]->theta) > 0.25 * M_PI) {
+        if (gs[i]->f64() || gs[i]->order != 2 || std::fabs(gs[i]->theta) > 0.25 * M_PI) {
             ts_status s = ts_evolve(gs[i], steps[i], K, stream);
             if (s != TS_OK) return s;
         } else {

@@ -8,6 +8,17 @@
 #include "../../include/trotter.h"
 #include "internal.h"
 
+namespace ts {
+// Kinetic rotation coefficients of one angle theta (FP64, rounded once where
+// used): versine form (g1 = 1 - cos theta, s1 = sin theta), lifting form
+// (t1 = tan(theta/2), s1) and the merged angle 2 theta (t2 = tan theta,
+// s2 = sin 2 theta).
+struct RotCoef {
+    double g1, s1, t1, s2, t2;
+};
+RotCoef rot_coef(double theta);
+}  // namespace ts
+
 // One grid: a slab of seven planes (re, im of ping-pong pairs 0 and 1,
 // gamma_V, s_V, V) plus reduction scratch; see ts_grid_layout.
 struct ts_grid {
@@ -18,6 +29,11 @@ struct ts_grid {
     int cur;                 // 0: planes 0/1 hold the state, 1: planes 2/3
     double dt, theta, J;
     double g1, s1, t1, s2, t2;   // rotation coefficients (FP64): theta and 2 theta
+    int order;                   // 2: U2(dt) per step; 4: U4(dt) (ts_set_potential_order)
+    ts::RotCoef sub[2];          // order 4: substeps p dt and (1 - 4p) dt
+    unsigned char *tab_b;        // order 4: (gamma_V, s_V) at (1 - 4p) dt, library-owned;
+                                 // planes 4/5 then hold the table at p dt
+    CUtensorMap tm_phase_b;
     double *partials, *result;
     int *err;
     bool tmaps_ok;
@@ -33,6 +49,8 @@ struct ts_grid {
     void *pg() const { return plane(4); }
     void *ps() const { return plane(5); }
     void *vp() const { return plane(6); }
+    void *pg_b() const { return tab_b; }
+    void *ps_b() const { return tab_b + L.plane_bytes; }
     bool f64() const { return L.dtype == TS_F64; }
 };
 

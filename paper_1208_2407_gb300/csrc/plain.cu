@@ -318,8 +318,8 @@ cudaError_t launch_phase_table(const double *V, void *pg, void *ps, void *vplane
     if (f64) {
         phase_table_kernel<double><<<grid, kThreads, 0, st>>>(V, (double *)pg, (double *)ps, (double *)vplane, nx, ny, pitch, dt);
     } else {
-        static TrigTable tab;
-        static double tab_dt = std::nan("");
+        thread_local TrigTable tab;   // per thread: grids may be prepared concurrently
+        thread_local double tab_dt = std::nan("");
         if (!(tab_dt == dt)) {   // host FP64 constants, split into double-floats
             const double pi_k = M_PI / 256.0;
             for (int k = 0; k < 256; ++k) {

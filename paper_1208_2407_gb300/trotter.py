@@ -86,6 +86,7 @@ _SIGNATURES = {
     "ts_set_state": [_VP, _VP, _VP, _INT, _INT, _VP],
     "ts_get_state": [_VP, _VP, _VP, _INT, _INT, _VP],
     "ts_set_potential": [_VP, _VP, _INT, _DBL, _DBL, _VP],
+    "ts_set_potential_order": [_VP, _VP, _INT, _DBL, _DBL, _INT, _VP],
     "ts_evolve": [_VP, _I64, _INT, _VP],
     "ts_evolve_plain": [_VP, _I64, _VP],
     "ts_observe": [_VP, ctypes.POINTER(ts_observables), _VP],
@@ -188,6 +189,10 @@ def ts_set_potential(h, v_ptr, where, dt, theta, stream):
 
 def ts_evolve(h, steps, K, stream):
     _call("ts_evolve", h, steps, K, stream)
+
+
+def ts_set_potential_order(h, v_ptr, where, dt, theta, order, stream):
+    _call("ts_set_potential_order", h, v_ptr, where, dt, theta, order, stream)
 
 
 def ts_evolve_plain(h, steps, stream):
@@ -362,22 +367,25 @@ class Grid:
                      stream or current_stream_ptr())
         return re, im
 
-    def set_potential(self, V, dt: float, theta: float, stream=None):
+    def set_potential(self, V, dt: float, theta: float, stream=None, order: int = 2):
+        """Phase table and kinetic coefficients for steps of length dt
+        (order 2: U2(dt); order 4: the fourth-order Suzuki step U4(dt))."""
         st = stream or current_stream_ptr()
+        args = (float(dt), float(theta), int(order), st)
         if V is None:
-            ts_set_potential(self.handle, None, TS_HOST, float(dt), float(theta), st)
+            ts_set_potential_order(self.handle, None, TS_HOST, *args)
             return
         torch = _torch()
         if isinstance(V, torch.Tensor):
             if V.dtype != torch.float64 or tuple(V.shape) != self.shape or not V.is_contiguous():
                 raise ValueError("V must be a contiguous float64 tensor of the grid's shape")
             where = TS_DEVICE if V.is_cuda else TS_HOST
-            ts_set_potential(self.handle, _VP(V.data_ptr()), where, float(dt), float(theta), st)
+            ts_set_potential_order(self.handle, _VP(V.data_ptr()), where, *args)
             return
         Va = np.ascontiguousarray(V, dtype=np.float64)
         if Va.shape != self.shape:
             raise ValueError("V must have the grid's shape")
-        ts_set_potential(self.handle, _VP(Va.ctypes.data), TS_HOST, float(dt), float(theta), st)
+        ts_set_potential_order(self.handle, _VP(Va.ctypes.data), TS_HOST, *args)
 
     def evolve(self, steps: int, K: int = 0, stream=None):
         ts_evolve(self.handle, int(steps), int(K), stream or current_stream_ptr())
