@@ -73,6 +73,9 @@ namespace {
 #ifndef TS_FUSED_MIN_BLOCKS_K3   // ... for K = 3: 168 registers, 12 one-warp blocks per SM
 #define TS_FUSED_MIN_BLOCKS_K3 9
 #endif
+#ifndef TS_FUSED_MIN_BLOCKS_K4   // ... for K = 4
+#define TS_FUSED_MIN_BLOCKS_K4 1
+#endif
 #ifndef TS_FUSED_PINGPONG_MIN_K  // interior row pairs alternate two carry sets for K in
 #define TS_FUSED_PINGPONG_MIN_K 3    // [MIN_K, MAX_K] (beyond MAX_K the second set spills)
 #endif
@@ -81,6 +84,9 @@ namespace {
 #endif
 #ifndef TS_FUSED_ALIGNED         // 1: strip-aligned work split when strips <= warps
 #define TS_FUSED_ALIGNED 1
+#endif
+#ifndef TS_FUSED_FFMA2           // packed FP32 FMAs (__ffma2_rn): see Cfg<K>::PACKED
+#define TS_FUSED_FFMA2 1
 #endif
 constexpr int PLANE_SLOT_BYTES = FUSED_BOX_ROWS * FUSED_BOX_COLS * 4;   // 1 KiB
 constexpr int SLOT_BYTES = 2 * PLANE_SLOT_BYTES;     // one ring slot: two planes of 2 rows
@@ -99,7 +105,12 @@ struct Cfg {
     static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
     static constexpr int PF = K == 1 ? TS_FUSED_PF_K1 : K == 2 ? TS_FUSED_PF_K2 : TS_FUSED_PF_DEEP;
     static constexpr bool PINGPONG = K >= TS_FUSED_PINGPONG_MIN_K && K <= TS_FUSED_PINGPONG_MAX_K;
-    static constexpr int MINB = K == 3 ? TS_FUSED_MIN_BLOCKS_K3 : TS_FUSED_MIN_BLOCKS;
+    static constexpr int MINB = K == 3   ? TS_FUSED_MIN_BLOCKS_K3
+                                : K == 4 ? TS_FUSED_MIN_BLOCKS_K4
+                                         : TS_FUSED_MIN_BLOCKS;
+    // packed FP32 FMAs in the Y sweeps and the phase: 0 never, 1 for every
+    // depth but 2 (where the scalar form measured faster), 2 always
+    static constexpr bool PACKED = TS_FUSED_FFMA2 == 2 || (TS_FUSED_FFMA2 == 1 && K != 2);
     static constexpr int NSS = PF + 1;
     static constexpr int NSP = PF + K + 1;
     static constexpr int HALO = ((2 * K + 3) / 4) * 4;
@@ -249,21 +260,77 @@ __device__ __forceinline__ void x_odd(Frag &f, const XOdd &c)
     rot1(f.re.x, f.im.x, pr, pi, c.gL, c.sL);
 }
 
+// Packed forms (Cfg<K>::PACKED): the column halves (x, y) and (z, w) of a
+// lane's float4 are register pairs, and __ffma2_rn applies one FMA to both
+// elements with the rounding of fmaf, so the results are bit for bit those of
+// the scalar forms with half the FMA instructions.  Used where the members
+// of every pair sit in the same column (Y sweeps, the phase).
+
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 join2(float2 lo, float2 hi)
+{
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// rot_lift on two columns at once; nt = (-t, -t), s2 = (s, s)
+__device__ __forceinline__ void rot_lift2(float2 &ar, float2 &ai, float2 &br, float2 &bi,
+                                          float2 nt, float2 s2)
+{
+    ar = __ffma2_rn(nt, bi, ar);
+    br = __ffma2_rn(nt, ai, br);
+    bi = __ffma2_rn(s2, ar, bi);
+    ai = __ffma2_rn(s2, br, ai);
+    ar = __ffma2_rn(nt, bi, ar);
+    br = __ffma2_rn(nt, ai, br);
+}
+
+// phase1 on two columns at once: r - g r + s m, m - g m - s r
+__device__ __forceinline__ void phase2(float2 &r, float2 &m, float2 g, float2 s)
+{
+    const float2 ng = make_float2(-g.x, -g.y), ns = make_float2(-s.x, -s.y);
+    const float2 nr = __ffma2_rn(s, m, __ffma2_rn(ng, r, r));
+    m = __ffma2_rn(ns, r, __ffma2_rn(ng, m, m));
+    r = nr;
+}
+
 // Y pair rotation of two rows (all four columns of the lane), lifting form.
+template <bool PACKED>
 __device__ __forceinline__ void y_pair(Frag &a, Frag &b, float t, float s)
 {
+    if constexpr (PACKED) {
+    const float2 nt = make_float2(-t, -t), s2 = make_float2(s, s);
+    float2 ar = lo2(a.re), ai = lo2(a.im), br = lo2(b.re), bi = lo2(b.im);
+    float2 cr = hi2(a.re), ci = hi2(a.im), dr = hi2(b.re), di = hi2(b.im);
+    rot_lift2(ar, ai, br, bi, nt, s2);
+    rot_lift2(cr, ci, dr, di, nt, s2);
+    a.re = join2(ar, cr);
+    a.im = join2(ai, ci);
+    b.re = join2(br, dr);
+    b.im = join2(bi, di);
+    } else {
     rot_lift(a.re.x, a.im.x, b.re.x, b.im.x, t, s);
     rot_lift(a.re.y, a.im.y, b.re.y, b.im.y, t, s);
     rot_lift(a.re.z, a.im.z, b.re.z, b.im.z, t, s);
     rot_lift(a.re.w, a.im.w, b.re.w, b.im.w, t, s);
+    }
 }
 
+template <bool PACKED>
 __device__ __forceinline__ void phase4(Frag &f, float4 g, float4 s)
 {
+    if constexpr (PACKED) {
+    float2 r0 = lo2(f.re), m0 = lo2(f.im), r1 = hi2(f.re), m1 = hi2(f.im);
+    phase2(r0, m0, lo2(g), lo2(s));
+    phase2(r1, m1, hi2(g), hi2(s));
+    f.re = join2(r0, r1);
+    f.im = join2(m0, m1);
+    } else {
     phase1(f.re.x, f.im.x, g.x, s.x);
     phase1(f.re.y, f.im.y, g.y, s.y);
     phase1(f.re.z, f.im.z, g.z, s.z);
     phase1(f.re.w, f.im.w, g.w, s.w);
+    }
 }
 
 __device__ __forceinline__ Frag zero_frag()
@@ -376,12 +443,12 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
     x_odd(b, c.O);
     {
         const bool v = yok(yin);
-        y_pair(a, b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+        y_pair<C::PACKED>(a, b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
     Frag P = cin[0], Q = a;       // rows (yin-1, yin)
     {
         const bool v = yok(yin - 1);
-        y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+        y_pair<C::PACKED>(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
     cout[0] = b;
     int y1 = yin - 1;
@@ -394,12 +461,12 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
     if (INTERIOR || j >= 1) {
         const unsigned char *sp = slot_p(1);
         const float4 sv = lds4(sp, 1, 1, lane);
-        phase4(P, lds4(sp, 0, 1, lane), MODE == 2 ? neg4(sv) : sv);
+        phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), MODE == 2 ? neg4(sv) : sv);
     }
     {
         const unsigned char *sp = slot_p(0);
         const float4 sv = lds4(sp, 1, 0, lane);
-        phase4(Q, lds4(sp, 0, 0, lane), MODE == 2 ? neg4(sv) : sv);
+        phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), MODE == 2 ? neg4(sv) : sv);
     }
     if constexpr (MODE == 1) {
         if (owns_row(w, p, y1)) mid_store(P, y1, w, p);
@@ -409,7 +476,7 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
     for (int k = 1; k < K; ++k) {
         {   // Yo (theta), aligned on (y1, y1+1), y1 odd
             const bool v = yok(y1);
-            y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+            y_pair<C::PACKED>(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
         }
         // X group between two phases: Xo, Xe(2 theta), Xo
         x_odd(P, c.O);
@@ -421,13 +488,13 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
         Frag P2 = cin[2 * k - 1], Q2 = P;     // rows (y1-1, y1)
         {   // Ye (2 theta), shifted: pair (y1-1, y1)
             const bool v = yok(y1 - 1);
-            y_pair(P2, Q2, v ? p.t2 : 0.f, v ? p.s2 : 0.f);
+            y_pair<C::PACKED>(P2, Q2, v ? p.t2 : 0.f, v ? p.s2 : 0.f);
         }
         cout[2 * k - 1] = Q;
         P = cin[2 * k];                       // rows (y1-2, y1-1)
         {   // Yo (theta), shifted: pair (y1-2, y1-1)
             const bool v = yok(y1 - 2);
-            y_pair(P, P2, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+            y_pair<C::PACKED>(P, P2, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
         }
         cout[2 * k] = Q2;
         Q = P2;
@@ -435,23 +502,23 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
         // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
         if (INTERIOR || j - k - 1 >= 0) {
             const unsigned char *sp = slot_p(k + 1);
-            phase4(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
+            phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
         }
         if (INTERIOR || j - k >= 0) {
             const unsigned char *sp = slot_p(k);
-            phase4(Q, lds4(sp, 0, 0, lane), lds4(sp, 1, 0, lane));
+            phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), lds4(sp, 1, 0, lane));
         }
     }
     // last step, second half: Yo aligned, Ye shifted, Xo, Xe
     {
         const bool v = yok(y1);
-        y_pair(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+        y_pair<C::PACKED>(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
     O0 = cin[2 * K - 1];      // rows (y1-1, y1) = (yin-2K, yin-2K+1)
     O1 = P;
     {
         const bool v = yok(y1 - 1);
-        y_pair(O0, O1, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+        y_pair<C::PACKED>(O0, O1, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
     cout[2 * K - 1] = Q;
     x_odd(O0, c.O);
