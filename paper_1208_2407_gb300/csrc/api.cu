@@ -36,9 +36,11 @@ ts_status cuda_fail(cudaError_t e, const char *what)
 
 constexpr int64_t kMaxSide = int64_t(1) << 20;
 
-// Depth of the fused path when the caller passes K = 0: the fastest on an
-// 8192^2 grid of one GB300 (site-steps/s: K=1 2.3e11, K=2 5.2e11, K=3 6.8e11,
-// K=4 6.5e11, K=6 5.7e11).
+// Depth of the fused path when the caller passes K = 0.  On one GB300 at
+// 8192^2 (site-steps/s): K=1 2.2e11, K=2 5.2e11, K=3 7.5e11, K=4 7.75e11,
+// K=5 7.2e11.  K = 3 runs at 88 % of the HBM copy bandwidth; K = 4 is 4 %
+// faster there but bound by instruction latency, so its speed follows the SM
+// clock (which drops under a power cap) while K = 3's follows HBM.
 int auto_depth() { return 3; }
 constexpr int kPlanes = 7;   // re_a, im_a, re_b, im_b, gamma_V, s_V, V
 
