@@ -52,6 +52,8 @@ def bind(lib):
         "oracle_step2": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double, ctypes.c_int],
         "oracle_evolve": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double, _I64,
                           ctypes.c_int, ctypes.c_int],
+        "oracle_evolve_driven": [_I64, _I64, _DP, _DP, _DP, _DP, _DP, ctypes.c_double,
+                                 ctypes.c_double, _I64, ctypes.c_int],
         "oracle_moments": [_I64, _I64, _DP, _DP, _DP],
         "oracle_energy": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, _DP],
         "oracle_inner": [_I64, _DP, _DP, _DP, _DP, _DP],
@@ -63,7 +65,7 @@ def bind(lib):
     }
     for name, args in sig.items():
         getattr(lib, name).argtypes = args
-    for name in ("oracle_evolve", "oracle_adjoint_grad"):
+    for name in ("oracle_evolve", "oracle_evolve_driven", "oracle_adjoint_grad"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("oracle_sweep_x", "oracle_sweep_y", "oracle_phase", "oracle_step2",
                  "oracle_moments", "oracle_energy", "oracle_inner", "oracle_apply_A",
@@ -130,6 +132,25 @@ def evolve(re, im, V, dt: float, theta: float, steps: int, order: int = 2,
                            int(steps), int(order), int(nthreads))
     if rc != 0:
         raise ValueError("oracle_evolve rejected its arguments (rc=%d)" % rc)
+    return re, im
+
+
+def evolve_driven(re, im, V0, V1, a, dt: float, theta: float, nthreads: int = 1):
+    """len(a) second-order steps with the potential V0 + a[n] V1 in step n
+    (the time-dependent extension of Sec. 2; a sampled at step midpoints)."""
+    lib = _load()
+    re, im = _state(re, im)
+    ny, nx = re.shape
+    V0c = None if V0 is None else _f64(V0)
+    V1c = None if V1 is None else _f64(V1)
+    for v in (V0c, V1c):
+        if v is not None and v.shape != re.shape:
+            raise ValueError("V0 and V1 must have the state's shape")
+    ac = _f64(np.ravel(a))
+    rc = lib.oracle_evolve_driven(nx, ny, _ptr(re), _ptr(im), _ptr(V0c), _ptr(V1c), _ptr(ac),
+                                  float(dt), float(theta), int(ac.size), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_evolve_driven rejected its arguments (rc=%d)" % rc)
     return re, im
 
 

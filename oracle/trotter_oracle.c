@@ -234,6 +234,30 @@ int oracle_evolve(int64_t nx, int64_t ny, double *re, double *im,
     return 0;
 }
 
+/* Time-dependent potential.  Sec. 2 writes the Schroedinger equation with a
+ * time-dependent H(t) and treats the time-independent case, noting that the
+ * time-dependent form is a direct extension.  Here V(t) = V0 + a(t) V1: step
+ * n is U2(dt) built with the potential V0 + a[n] V1, where the caller gives
+ * a[n] (sampling a(t) at the middle of the step, t = (n + 1/2) dt, keeps the
+ * step second order in time).  V0 or V1 may be NULL (zero).  Returns 0 on
+ * success, -1 on a bad argument or allocation failure. */
+int oracle_evolve_driven(int64_t nx, int64_t ny, double *re, double *im,
+                         const double *V0, const double *V1, const double *a,
+                         double dt, double theta, int64_t steps, int nthreads)
+{
+    if (nx < 1 || ny < 1 || steps < 0 || !re || !im || (steps > 0 && !a)) return -1;
+    const int64_t n = nx * ny;
+    double *Vn = (double *)malloc((size_t)n * sizeof(double));
+    if (!Vn) return -1;
+    for (int64_t s = 0; s < steps; ++s) {
+        for (int64_t i = 0; i < n; ++i)
+            Vn[i] = (V0 ? V0[i] : 0.0) + a[s] * (V1 ? V1[i] : 0.0);
+        oracle_step2(nx, ny, re, im, Vn, dt, theta, nthreads);
+    }
+    free(Vn);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Observables (Sec. 2: the norm <psi|psi> is conserved by the unitary U).    */
 /* All sums use Neumaier's compensated summation.                            */

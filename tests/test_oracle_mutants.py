@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 
+import test_oracle_drive as drive
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "trotter_oracle.c")
@@ -42,6 +43,10 @@ MUTANTS = [
     ("adjoint_half", "            nsum_add(&acc[j], 2.0 * dt * zi);", "            nsum_add(&acc[j], dt * zi);"),
     ("energy_no_vertical_bonds", "            if (y + 1 < ny) {\n                int64_t k = i + nx;",
      "            if (0) {\n                int64_t k = i + nx;"),
+    ("drive_first_amplitude_only", "            Vn[i] = (V0 ? V0[i] : 0.0) + a[s] * (V1 ? V1[i] : 0.0);",
+     "            Vn[i] = (V0 ? V0[i] : 0.0) + a[0] * (V1 ? V1[i] : 0.0);"),
+    ("drive_sign", "            Vn[i] = (V0 ? V0[i] : 0.0) + a[s] * (V1 ? V1[i] : 0.0);",
+     "            Vn[i] = (V0 ? V0[i] : 0.0) - a[s] * (V1 ? V1[i] : 0.0);"),
     ("uncompensated_sum", "    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;\n    else a->c += (v - t) + a->s;\n",
      ""),
 ]
@@ -59,6 +64,8 @@ PIN_CHECKS = [
     pins.test_energy_equals_dense_expectation,
     pins.test_compensated_sum_is_exactly_rounded_on_cancellation,
     lambda: pins.test_adjoint_matches_finite_differences(6, 5, 12),
+    drive.test_driven_steps_equal_dense_products,
+    drive.test_uniform_drive_is_a_global_phase,
 ]
 
 
