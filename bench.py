@@ -54,8 +54,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-requests", type=int, default=512)
-    ap.add_argument("--order4", action="store_true",
-                    help="time fourth-order steps (prints its own JSON line)")
+    ap.add_argument("--variants", action="store_true",
+                    help="time fourth-order steps and a time-dependent potential instead "
+                         "(prints its own JSON line)")
     ap.add_argument("--paper", action="store_true",
                     help="time the paper's single-node sizes instead (L = 24576 FP32, "
                          "17472 FP64, flat V, ten iterations)")
@@ -539,30 +540,37 @@ def paper_sizes(args):
     return 0
 
 
-def fourth_order(args):
-    """Fourth-order steps (U4 = five second-order substeps) on the n x n
-    random-Gaussian workload: site-steps/s counted in U4 steps, for a few
-    depths, beside second order at the same number of substeps."""
+def method_variants(args):
+    """The method's variants on the n x n random-Gaussian workload, inputs
+    resident in HBM: second order (the default depth), fourth-order steps U4
+    (five second-order substeps; counted per U4 step) at a few depths, and a
+    time-dependent potential V0 + a(t) V1 (a field along x oscillating in
+    time; the drive phase is computed per site and step on the device)."""
     import torch
     from paper_1208_2407_gb300 import trotter
     from paper_1208_2407_gb300 import workloads as wl
     torch.cuda.set_device(0)
     trotter.load()
     n = args.n
-    T4 = max(1, args.trotter_steps // 5)
-    c = wl.roofline_grid(n=n, seed=args.seed, steps=T4)
+    T = args.trotter_steps
+    T4 = max(1, T // 5)
+    c = wl.roofline_grid(n=n, seed=args.seed, steps=T)
     re0 = torch.from_numpy(c["re"].astype(np.float32)).cuda()
     im0 = torch.from_numpy(c["im"].astype(np.float32)).cuda()
     Vd = torch.from_numpy(c["V"]).cuda()
+    V1 = torch.arange(n, dtype=torch.float64, device="cuda").sub_(n / 2.0).expand(n, n).contiguous()
+    amp = 1e-3 * np.cos(0.05 * (np.arange(T) + 0.5) * c["dt"])
     g = trotter.Grid(n, n, "f32")
     runs = []
-    for order, K, steps in ((4, 0, T4), (4, 3, T4), (4, 2, T4), (2, 0, 5 * T4)):
-        g.set_state(re0, im0)
-        g.set_potential(Vd, c["dt"], c["theta"], order=order)
-        g.evolve(steps, K)
+    cases = (("order 2", 2, 0, T, False), ("order 4", 4, 0, T4, False), ("order 4", 4, 3, T4, False),
+             ("drive", 2, 0, T, True), ("drive", 2, 4, T, True))
+    for name, order, K, steps, drive in cases:
         ms = []
-        for _ in range(max(1, args.steps)):
+        for rep in range(max(1, args.steps) + 1):
             g.set_state(re0, im0)
+            g.set_potential(Vd, c["dt"], c["theta"], order=order)
+            if drive:
+                g.set_drive(V1, amp[:steps])
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             trotter.ts_launch_count(reset=True)
@@ -570,16 +578,17 @@ def fourth_order(args):
             g.evolve(steps, K)
             b.record()
             torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
+            if rep > 0:                  # the first run is a warm-up
+                ms.append(a.elapsed_time(b))
         t = float(np.median(ms))
         substeps = steps * (5 if order == 4 else 1)
-        runs.append({"order": order, "K": K, "steps": steps, "ms": t,
+        runs.append({"variant": name, "order": order, "K": K, "steps": steps, "ms": t,
                      "launches": trotter.ts_launch_count(),
                      "site_steps_per_s": float(n) * n * steps / (t / 1e3),
                      "site_substeps_per_s": float(n) * n * substeps / (t / 1e3),
                      "norm": g.norm()})
     g.close()
-    print(json.dumps({"metric": "fourth-order site-steps/s", "n": n, "runs": runs,
+    print(json.dumps({"metric": "site-steps/s of the method's variants", "n": n, "runs": runs,
                       "data": "synthetic", "inputs": "resident in HBM"}), flush=True)
     return 0
 
@@ -588,8 +597,8 @@ def main():
     args = parse()
     if args.paper:
         return paper_sizes(args)
-    if args.order4:
-        return fourth_order(args)
+    if args.variants:
+        return method_variants(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

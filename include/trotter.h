@@ -131,6 +131,35 @@ ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
 ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, double dt,
                                  double theta, int order, void *stream);
 
+/* Time-dependent potential (Sec. 2 writes the Schroedinger equation with a
+ * time-dependent H(t); the time-dependent form of the method is an
+ * extension of the time-independent one the paper details):
+ *     V(x, y, t) = V0(x, y) + a(t) V1(x, y).
+ * V0, dt and theta are those of the last ts_set_potential, which must come
+ * first (and a later ts_set_potential or ts_set_potential_order ends the
+ * drive).  V1: dense FP64 array of nx*ny values in host or device memory,
+ * or NULL (zero); stored in the grid's dtype.  a: host array of n_a
+ * amplitudes, copied; the n-th step evolved after this call uses a[n] in
+ * its phase exp(-i (V0 + a[n] V1) dt).  Sampling a(t) at the middle of
+ * each step, a[n] = a((n + 1/2) dt) from the time the drive starts, keeps
+ * the step second order in time.  ts_evolve and ts_evolve_plain then fail
+ * with TS_ERR_ARG, before launching anything, if they are asked for more
+ * steps than amplitudes are left.  The drive phase exp(-i a[n] dt V1) is
+ * computed on the device per site and step (no table); the fused path runs
+ * at depth <= 4.  Needs three more planes of ts_layout.plane_bytes,
+ * cudaMalloc'd by the library on first use and freed by ts_destroy_grid.
+ * ts_observe's e_pot is sum V0 |psi|^2 (without the drive term).  Driven
+ * grids are evolved one by one by ts_evolve_batched and refused by the
+ * adjoint calls.  Errors: TS_ERR_ARG (NULL grid, bad or non-finite a),
+ * TS_ERR_UNSUPPORTED (grid set to order 4), TS_ERR_OOM, TS_ERR_CUDA.
+ * Async for device V1 (host V1: returns when it may be reused). */
+ts_status ts_set_drive(ts_grid *g, const double *V1, ts_mem where, const double *a,
+                       int64_t n_a, void *stream);
+
+/* End the drive: later steps use V0 alone.  The drive planes stay
+ * allocated until ts_destroy_grid. */
+ts_status ts_clear_drive(ts_grid *g);
+
 /* Evolve `steps` second-order steps (Eq. secondorder) on the grid's current
  * state.  FP32 grids run the fused kernel: K whole steps per HBM round trip
  * on TMA-staged shared-memory tiles (temporal blocking; K = 0 picks the

@@ -81,6 +81,9 @@ ts_status grid_setup(const ts_layout &L, void *slab, bool owns_slab, ts_grid **o
     g->order = 2;
     g->sub[0] = g->sub[1] = RotCoef{0.0, 0.0, 0.0, 0.0, 0.0};
     g->tab_b = nullptr;
+    g->drive_slab = nullptr;
+    g->drive_pos = 0;
+    g->driven = false;
     g->tmaps_ok = false;
     if (L.dtype == TS_F32) {
         const char *why = "";
@@ -293,8 +296,9 @@ ts_status ts_destroy_grid(ts_grid *g)
     ts::forget_adjoint(g);
     cudaError_t e = cudaSuccess;
     if (g->owns_slab) e = cudaFree(g->slab);
-    if (g->tab_b) {
-        cudaError_t f = cudaFree(g->tab_b);
+    for (unsigned char *extra : {g->tab_b, g->drive_slab}) {
+        if (!extra) continue;
+        cudaError_t f = cudaFree(extra);
         if (e == cudaSuccess) e = f;
     }
     delete g;
@@ -453,6 +457,8 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
     if (order != 2 && order != 4)
         return fail(TS_ERR_ARG, "ts_set_potential_order: order must be 2 or 4, got %d", order);
     cudaStream_t st = (cudaStream_t)stream;
+    g->driven = false;   // a new potential ends any time-dependent drive
+    g->drive_a.clear();
     const int nx = (int)g->L.nx, ny = (int)g->L.ny;
     cudaError_t e;
     // fourth order (Eq. fourthorder): U4(dt) = U2(p dt)^2 U2((1-4p) dt) U2(p dt)^2
@@ -505,12 +511,75 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
     return TS_OK;
 }
 
+ts_status ts_set_drive(ts_grid *g, const double *V1, ts_mem where, const double *a, int64_t n_a,
+                       void *stream)
+{
+    if (!g) return fail(TS_ERR_ARG, "ts_set_drive: grid is NULL");
+    if (n_a < 0 || (n_a > 0 && !a)) return fail(TS_ERR_ARG, "ts_set_drive: bad amplitude array");
+    if (where != TS_HOST && where != TS_DEVICE)
+        return fail(TS_ERR_ARG, "ts_set_drive: unknown memory kind");
+    if (g->order != 2) return fail(TS_ERR_UNSUPPORTED, "ts_set_drive: second-order grids only");
+    for (int64_t i = 0; i < n_a; ++i)
+        if (!std::isfinite(a[i])) return fail(TS_ERR_ARG, "ts_set_drive: a[%lld] is not finite", (long long)i);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    const size_t PB = g->L.plane_bytes;
+    cudaError_t e;
+    if (!g->drive_slab) {
+        unsigned char *ds = nullptr;
+        e = cudaMalloc((void **)&ds, 3 * PB);
+        if (e != cudaSuccess)
+            return fail(TS_ERR_OOM, "ts_set_drive: drive planes: %s", cudaGetErrorString(e));
+        if (!g->f64()) {
+            const char *why = "";
+            if (!ts::make_pair_tensor_map(&g->tm_drive, ds, nx, ny, g->L.pitch, PB, &why, 3)) {
+                cudaFree(ds);
+                return fail(TS_ERR_CUDA, "ts_set_drive: %s", why);
+            }
+        }
+        g->drive_slab = ds;
+    }
+    // the static table (gamma_V, s_V) next to V1, so one box load fetches all three
+    e = cudaMemcpyAsync(g->drive_slab, g->pg(), 2 * PB, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ts_set_drive: table copy");
+    if (!V1) {
+        e = cudaMemsetAsync(g->drive_v1(), 0, PB, st);
+    } else {
+        const double *src = V1;
+        if (where == TS_HOST) {
+            e = cudaMemcpyAsync(g->re_other(), V1, (size_t)nx * ny * sizeof(double),
+                                cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "ts_set_drive: host-to-device copy");
+            src = (const double *)g->re_other();
+        }
+        e = ts::launch_convert_in(src, true, g->drive_v1(), g->f64(), nx, ny, g->L.pitch, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "ts_set_drive: V1");
+    if (where == TS_HOST) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "ts_set_drive");
+    }
+    g->drive_a.assign(a, a + n_a);
+    g->drive_pos = 0;
+    g->driven = true;
+    return TS_OK;
+}
+
+ts_status ts_clear_drive(ts_grid *g)
+{
+    if (!g) return fail(TS_ERR_ARG, "ts_clear_drive: grid is NULL");
+    g->driven = false;
+    g->drive_a.clear();
+    g->drive_pos = 0;
+    return TS_OK;
+}
+
 namespace {
 
 // `steps` second-order steps, one kernel per sweep, with the rotation
 // coefficients c and the phase table (pg, ps).
 ts_status plain_run(ts_grid *g, int64_t steps, const ts::RotCoef &c, const void *pg,
-                    const void *ps, cudaStream_t st)
+                    const void *ps, cudaStream_t st, const double *drive_adt = nullptr)
 {
     const int nx = (int)g->L.nx, ny = (int)g->L.ny;
     const int64_t pitch = g->L.pitch;
@@ -528,6 +597,8 @@ ts_status plain_run(ts_grid *g, int64_t steps, const ts::RotCoef &c, const void 
             e = ts::launch_plain_sweep(re, im, f, nx, ny, pitch, seq_axis[i], seq_par[i], gg, ss, st);
         if (e == cudaSuccess)
             e = ts::launch_plain_phase(re, im, pg, ps, f, nx, ny, pitch, st);
+        if (e == cudaSuccess && drive_adt)
+            e = ts::launch_plain_drive(re, im, g->drive_v1(), f, nx, ny, pitch, drive_adt[n], st);
         for (int i = 3; i >= 0 && e == cudaSuccess; --i)
             e = ts::launch_plain_sweep(re, im, f, nx, ny, pitch, seq_axis[i], seq_par[i], gg, ss, st);
         if (e != cudaSuccess) return cuda_fail(e, "plain sweep launch");
@@ -540,7 +611,7 @@ ts_status plain_run(ts_grid *g, int64_t steps, const ts::RotCoef &c, const void 
 // `steps` second-order steps on the fused path at depth K (a remainder runs
 // at a smaller depth), with the coefficients c and the phase table map tm.
 ts_status fused_run(ts_grid *g, int64_t steps, int K, const ts::RotCoef &c,
-                    const CUtensorMap *tm, cudaStream_t st)
+                    const CUtensorMap *tm, cudaStream_t st, const double *drive_adt = nullptr)
 {
     if (!g->tmaps_ok) return fail(TS_ERR_STATE, "fused path: tensor maps missing");
     int64_t left = steps;
@@ -560,7 +631,13 @@ ts_status fused_run(ts_grid *g, int64_t steps, int K, const ts::RotCoef &c,
         a.t2 = (float)c.t2;
         a.s2 = (float)c.s2;
         a.err = g->err;
-        cudaError_t e = ts::launch_fused(k, a, st);
+        cudaError_t e;
+        if (drive_adt) {
+            for (int i = 0; i < k; ++i) a.adt[i] = (float)drive_adt[steps - left + i];
+            e = ts::launch_fused_drive(k, a, st);
+        } else {
+            e = ts::launch_fused(k, a, st);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
         g->cur ^= 1;
         left -= k;
@@ -585,6 +662,29 @@ ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
 // neighbouring steps run back to back (a run of 2 at either end, of 4
 // between two b substeps), so on the fused path each run of r substeps is
 // ceil(r / K) launches of near-equal depth; each b substep is one launch.
+// Steps with the time-dependent potential V0 + a_n V1: the next `steps`
+// amplitudes, each multiplied by dt; the fused kernel at depth <= 4 or,
+// for FP64 grids and |theta| > pi/4, the plain path.
+ts_status evolve_driven(ts_grid *g, int64_t steps, int K, bool plain, cudaStream_t st)
+{
+    const int64_t left = (int64_t)g->drive_a.size() - g->drive_pos;
+    if (steps > left)
+        return fail(TS_ERR_ARG, "ts_evolve: %lld steps asked for but %lld drive amplitudes are left",
+                    (long long)steps, (long long)left);
+    std::vector<double> adt((size_t)steps);
+    for (int64_t i = 0; i < steps; ++i) adt[(size_t)i] = g->drive_a[(size_t)(g->drive_pos + i)] * g->dt;
+    ts_status s;
+    if (plain) {
+        s = plain_run(g, steps, grid_coef(g), g->pg(), g->ps(), st, adt.data());
+    } else {
+        int depth = K == 0 ? auto_depth() : K;
+        if (depth > ts::FUSED_DRIVE_MAX_K) depth = ts::FUSED_DRIVE_MAX_K;
+        s = fused_run(g, steps, depth, grid_coef(g), &g->tm_drive, st, adt.data());
+    }
+    if (s == TS_OK) g->drive_pos += steps;
+    return s;
+}
+
 ts_status evolve4(ts_grid *g, int64_t steps, int K, bool plain, cudaStream_t st)
 {
     const int depth = K == 0 ? 4 : K;
@@ -621,6 +721,8 @@ ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     if (g->f64() && K != 0)
         return fail(TS_ERR_UNSUPPORTED, "ts_evolve: FP64 grids run the plain path (K must be 0)");
+    if (g->driven)
+        return evolve_driven(g, steps, K, g->f64() || std::fabs(g->theta) > 0.25 * M_PI, st);
     if (g->order == 4) {
         // the substep angles p theta and (1-4p) theta must both suit the fused kernel
         const double p4 = 1.0 / (4.0 - std::cbrt(4.0));
@@ -641,6 +743,7 @@ ts_status ts_evolve_plain(ts_grid *g, int64_t steps, void *stream)
     if (!g) return fail(TS_ERR_ARG, "ts_evolve_plain: grid is NULL");
     if (steps < 0) return fail(TS_ERR_ARG, "ts_evolve_plain: negative step count");
     if (steps == 0) return TS_OK;
+    if (g->driven) return evolve_driven(g, steps, 0, true, (cudaStream_t)stream);
     if (g->order == 4) return evolve4(g, steps, 0, true, (cudaStream_t)stream);
     return plain_steps(g, steps, (cudaStream_t)stream);
 }
@@ -651,14 +754,15 @@ ts_status ts_evolve_batched(ts_grid *const *gs, int n, const int64_t *steps, int
     if (K < 0 || K > ts::FUSED_MAX_K) return fail(TS_ERR_ARG, "ts_evolve_batched: K must be in [0, 8]");
     cudaStream_t st = (cudaStream_t)stream;
     const int depth = K == 0 ? auto_depth() : K;
-    // grids the multi-grid kernel can take: FP32, second order, |theta| <=
-    // pi/4; the rest evolve one by one
+    // grids the multi-grid kernel can take: FP32, second order, no drive,
+    // |theta| <= pi/4; the rest evolve one by one
     std::vector<ts_grid *> multi;
     std::vector<int64_t> msteps;
     for (int i = 0; i < n; ++i) {
         if (!gs[i] || steps[i] < 0) return fail(TS_ERR_ARG, "ts_evolve_batched: grid %d", i);
         if (steps[i] == 0) continue;
-        if (gs[i]->f64() || gs[i]->order != 2 || std::fabs(gs[i]->theta) > 0.25 * M_PI) {
+        if (gs[i]->f64() || gs[i]->order != 2 || gs[i]->driven ||
+            std::fabs(gs[i]->theta) > 0.25 * M_PI) {
             ts_status s = ts_evolve(gs[i], steps[i], K, stream);
             if (s != TS_OK) return s;
         } else {

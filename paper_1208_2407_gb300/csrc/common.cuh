@@ -44,6 +44,37 @@ __device__ __forceinline__ void phase1(T &r, T &m, T g, T s)
     m = nm;
 }
 
+// Versine coefficients of an angle phi computed on the device in FP32:
+// g = 1 - cos phi = 2 sin^2 h, s = sin phi = 2 sin h cos h with h = phi/2.
+// For |h| <= 0.4, sin h and cos h come from their Taylor series through h^7
+// and h^8 (truncation below 2e-9 relative, under half an FP32 ulp); larger
+// angles call sincosf.  g and s share sin h and cos h, so
+// (1 - g)^2 + s^2 - 1 = -4 sin^2 h (1 - sin^2 h - cos^2 h) stays at
+// O(ulp * phi^2): the unitarity defect shrinks with the angle.
+__device__ __forceinline__ void angle_versine(float phi, float &g, float &s)
+{
+    const float h = 0.5f * phi;
+    float sh, ch;
+    if (fabsf(h) <= 0.4f) {
+        const float h2 = h * h;
+        sh = h * fmaf(h2, fmaf(h2, fmaf(h2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+        ch = fmaf(h2, fmaf(h2, fmaf(h2, fmaf(h2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f),
+                           -0.5f), 1.0f);
+    } else {
+        sincosf(h, &sh, &ch);
+    }
+    g = 2.0f * sh * sh;
+    s = 2.0f * sh * ch;
+}
+
+// The same in FP64 (plain path of FP64 grids).
+__device__ __forceinline__ void angle_versine(double phi, double &g, double &s)
+{
+    const double sh = sin(0.5 * phi);
+    g = 2.0 * sh * sh;
+    s = sin(phi);
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {
     uint64_t t;

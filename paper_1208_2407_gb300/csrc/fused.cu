@@ -100,7 +100,7 @@ constexpr uint32_t FULL = 0xffffffffu;
 //    last one K row pairs later, so it needs PF + K + 1 slots.
 // Shallow pipelines (K <= 2) are memory bound and prefetch deeper; deep ones
 // are arithmetic bound and keep shared memory small for occupancy.
-template <int K>
+template <int K, bool DRIVE = false>
 struct Cfg {
     static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
     static constexpr int PF = K == 1 ? TS_FUSED_PF_K1 : K == 2 ? TS_FUSED_PF_K2 : TS_FUSED_PF_DEEP;
@@ -115,7 +115,9 @@ struct Cfg {
     static constexpr int NSP = PF + K + 1;
     static constexpr int HALO = ((2 * K + 3) / 4) * 4;
     static constexpr int VALID = FUSED_BOX_COLS - 2 * HALO;
-    static constexpr int WARP_SMEM = (NSS + NSP) * SLOT_BYTES;
+    // a phase slot holds (gamma_V, s_V) and, with a drive, the V1 rows too
+    static constexpr int PSLOT = (DRIVE ? 3 : 2) * PLANE_SLOT_BYTES;
+    static constexpr int WARP_SMEM = NSS * SLOT_BYTES + NSP * PSLOT;
     static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + (NSS + NSP) * 8);
 };
 
@@ -139,6 +141,9 @@ struct KParams {
     // double-float planes (g_rh + g_rl, g_ih + g_il)
     float *m_re, *m_im;
     float *g_rh, *g_rl, *g_ih, *g_il;
+    // MODE 3 (time-dependent potential V0 + a(t) V1): a_n dt of step k of
+    // the launch; the phase ring carries V1 as a third plane
+    float adt[FUSED_MAX_K];
 };
 
 // ---- PTX wrappers ---------------------------------------------------------
@@ -333,6 +338,19 @@ __device__ __forceinline__ void phase4(Frag &f, float4 g, float4 s)
     }
 }
 
+// Drive phase exp(-i a dt V1) of one row of the lane (time-dependent
+// potential): adt = a_n dt of the step, v1 = the row's V1 values.
+template <bool PACKED>
+__device__ __forceinline__ void drive4(Frag &f, float4 v1, float adt)
+{
+    float4 g, s;
+    angle_versine(adt * v1.x, g.x, s.x);
+    angle_versine(adt * v1.y, g.y, s.y);
+    angle_versine(adt * v1.z, g.z, s.z);
+    angle_versine(adt * v1.w, g.w, s.w);
+    phase4<PACKED>(f, g, s);
+}
+
 __device__ __forceinline__ Frag zero_frag()
 {
     Frag f;
@@ -427,14 +445,14 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
                                               const StripCoef &c, const KParams &p, int lane,
                                               const Owned &w, Frag &O0, Frag &O1)
 {
-    static_assert(MODE == 0 || K == 1, "mid-step modes exist for K = 1 only");
-    using C = Cfg<K>;
+    static_assert(MODE == 0 || MODE == 3 || K == 1, "mid-step modes exist for K = 1 only");
+    using C = Cfg<K, MODE == 3>;
     constexpr int NSP = C::NSP;
     auto yok = [&](int y) { return INTERIOR || (y >= 0 && y + 1 < p.ny); };
     auto slot_p = [&](int back) -> const unsigned char * {   // phase slot j - back
         int q = pos_p - back;
         if (q < 0) q += NSP;
-        return ring_p + q * SLOT_BYTES;
+        return ring_p + q * C::PSLOT;
     };
     // step 0, first half: Xe, Xo (row-local), Ye aligned, Yo shifted
     x_even(a, c.E1);
@@ -462,11 +480,13 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
         const unsigned char *sp = slot_p(1);
         const float4 sv = lds4(sp, 1, 1, lane);
         phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), MODE == 2 ? neg4(sv) : sv);
+        if constexpr (MODE == 3) drive4<C::PACKED>(P, lds4(sp, 2, 1, lane), p.adt[0]);
     }
     {
         const unsigned char *sp = slot_p(0);
         const float4 sv = lds4(sp, 1, 0, lane);
         phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), MODE == 2 ? neg4(sv) : sv);
+        if constexpr (MODE == 3) drive4<C::PACKED>(Q, lds4(sp, 2, 0, lane), p.adt[0]);
     }
     if constexpr (MODE == 1) {
         if (owns_row(w, p, y1)) mid_store(P, y1, w, p);
@@ -503,10 +523,12 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
         if (INTERIOR || j - k - 1 >= 0) {
             const unsigned char *sp = slot_p(k + 1);
             phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
+            if constexpr (MODE == 3) drive4<C::PACKED>(P, lds4(sp, 2, 1, lane), p.adt[k]);
         }
         if (INTERIOR || j - k >= 0) {
             const unsigned char *sp = slot_p(k);
             phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), lds4(sp, 1, 0, lane));
+            if constexpr (MODE == 3) drive4<C::PACKED>(Q, lds4(sp, 2, 0, lane), p.adt[k]);
         }
     }
     // last step, second half: Yo aligned, Ye shifted, Xo, Xe
@@ -537,10 +559,10 @@ struct WarpRings {
     uint32_t par_s, par_p;
 };
 
-template <int K>
+template <int K, bool DRIVE = false>
 __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int warp, int lane)
 {
-    using C = Cfg<K>;
+    using C = Cfg<K, DRIVE>;
     constexpr int NSS = C::NSS, NSP = C::NSP;
     WarpRings r;
     // barriers first, then 1 KiB-aligned slots (state ring, phase ring)
@@ -581,11 +603,12 @@ __device__ __forceinline__ void issue_state(WarpRings &r, const Seg &s, int pos,
     tma_load_pair(r.ring_s + pos * SLOT_BYTES, s.tm_state, s.XL, s.Ys + 2 * j, &r.bar_s[pos]);
 }
 
-template <int K>
+template <int K, bool DRIVE = false>
 __device__ __forceinline__ void issue_phase(WarpRings &r, const Seg &s, int pos, int j)
 {
-    mbar_expect_tx(&r.bar_p[pos], SLOT_BYTES);
-    tma_load_pair(r.ring_p + pos * SLOT_BYTES, s.tm_phase, s.XL, s.Ys + 2 * j, &r.bar_p[pos]);
+    constexpr int PSLOT = Cfg<K, DRIVE>::PSLOT;
+    mbar_expect_tx(&r.bar_p[pos], PSLOT);
+    tma_load_pair(r.ring_p + pos * PSLOT, s.tm_phase, s.XL, s.Ys + 2 * j, &r.bar_p[pos]);
 }
 
 // Row pair j of a segment: wait for its slots, run the pipeline, store the
@@ -596,7 +619,7 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
                                          const Frag (&cin)[2 * K], Frag (&cout)[2 * K],
                                          int &issued_s, int &issued_p)
 {
-    using C = Cfg<K>;
+    using C = Cfg<K, MODE == 3>;
     constexpr int NSS = C::NSS, NSP = C::NSP;
     const int lane = s.lane;
     bool ok = mbar_wait(&r.bar_s[r.pos_s], r.par_s, WAIT_LIMIT_NS) &&
@@ -646,7 +669,8 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     if (lane == 0 && (more_s || more_p)) {
         fence_proxy_async();
         if (more_s) issue_state<K>(r, s, r.pos_s, js);
-        if (more_p) issue_phase<K>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
+        if (more_p)
+            issue_phase<K, MODE == 3>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
     }
     issued_s += more_s;
     issued_p += more_p;
@@ -663,7 +687,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
                                             const CUtensorMap *tm_phase, const KParams &p,
                                             int sx, int q0, int q1, int lane)
 {
-    using C = Cfg<K>;
+    using C = Cfg<K, MODE == 3>;
     constexpr int NSS = C::NSS, NSP = C::NSP, HALO = C::HALO, VALID = C::VALID;
     Seg s;
     s.tm_state = tm_state;
@@ -694,7 +718,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
         fence_proxy_async();
         for (int j = 0; j < n_pro_p; ++j) {
             if (j < n_pro_s) issue_state<K>(r, s, (r.pos_s + j) % NSS, j);
-            issue_phase<K>(r, s, (r.pos_p + j) % NSP, j);
+            issue_phase<K, MODE == 3>(r, s, (r.pos_p + j) % NSP, j);
         }
     }
     int issued_s = n_pro_s, issued_p = n_pro_p;
@@ -742,7 +766,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * Cfg<K>::WPC + warp;
     if (gw >= p.total_warps) return;
-    WarpRings r = carve_rings<K>(smem_raw, warp, lane);
+    WarpRings r = carve_rings<K, MODE == 3>(smem_raw, warp, lane);
     if (p.strip_warps > 0) {
         // strip-aligned split: warp (sx, i) takes row range i of strip sx, so
         // warps of neighbouring strips walk the same rows at the same time and
@@ -827,7 +851,7 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
 template <int K, int MODE>
 cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
 {
-    using C = Cfg<K>;
+    using C = Cfg<K, MODE == 3>;
     static int blocks_per_sm = -1;
     static int num_sms = 0;
     if (blocks_per_sm < 0) {
@@ -876,6 +900,7 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.g_rl = a.g_rl;
     p.g_ih = a.g_ih;
     p.g_il = a.g_il;
+    for (int k = 0; k < FUSED_MAX_K; ++k) p.adt[k] = a.adt[k];
     const int blocks = (p.total_warps + C::WPC - 1) / C::WPC;
     fused_kernel<K, MODE><<<blocks, C::WPC * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
     count_launches(1);
@@ -984,6 +1009,17 @@ cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, int64_
     }
 }
 
+cudaError_t launch_fused_drive(int K, const FusedLaunch &a, cudaStream_t st)
+{
+    switch (K) {
+    case 1: return launch_k<1, 3>(a, st);
+    case 2: return launch_k<2, 3>(a, st);
+    case 3: return launch_k<3, 3>(a, st);
+    case 4: return launch_k<4, 3>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st)
 {
     if (mode == 1) return launch_k<1, 1>(a, st);
@@ -992,7 +1028,7 @@ cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st)
 }
 
 bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
-                          size_t plane_bytes, const char **why)
+                          size_t plane_bytes, const char **why, int planes)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -1006,9 +1042,13 @@ bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int
         }
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 2};
+    if (planes < 1 || planes > 3) {
+        *why = "tensor map: 1 to 3 planes";
+        return false;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)(pitch * 4), (cuuint64_t)plane_bytes};
-    cuuint32_t box[3] = {FUSED_BOX_COLS, FUSED_BOX_ROWS, 2};
+    cuuint32_t box[3] = {FUSED_BOX_COLS, FUSED_BOX_ROWS, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

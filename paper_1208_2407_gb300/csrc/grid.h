@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda.h>
+#include <vector>
 
 #include "../../include/trotter.h"
 #include "internal.h"
@@ -34,6 +35,14 @@ struct ts_grid {
     unsigned char *tab_b;        // order 4: (gamma_V, s_V) at (1 - 4p) dt, library-owned;
                                  // planes 4/5 then hold the table at p dt
     CUtensorMap tm_phase_b;
+    // time-dependent potential V0 + a_n V1 (ts_set_drive): a library-owned
+    // slab of three planes (copies of gamma_V, s_V, then V1), its tensor map,
+    // the amplitudes a_n and the index of the next one
+    unsigned char *drive_slab;
+    CUtensorMap tm_drive;
+    std::vector<double> drive_a;
+    int64_t drive_pos;
+    bool driven;
     double *partials, *result;
     int *err;
     bool tmaps_ok;
@@ -49,6 +58,7 @@ struct ts_grid {
     void *pg() const { return plane(4); }
     void *ps() const { return plane(5); }
     void *vp() const { return plane(6); }
+    void *drive_v1() const { return drive_slab + 2 * L.plane_bytes; }
     void *pg_b() const { return tab_b; }
     void *ps_b() const { return tab_b + L.plane_bytes; }
     bool f64() const { return L.dtype == TS_F64; }

@@ -34,6 +34,10 @@ cudaError_t launch_plain_sweep(void *re, void *im, bool f64, int nx, int ny, int
 // the diagonal phase exp(-i V dt) from the stored table, in place
 cudaError_t launch_plain_phase(void *re, void *im, const void *pg, const void *ps, bool f64,
                                int nx, int ny, int64_t pitch, cudaStream_t st);
+// psi <- psi exp(-i adt V1) (the drive term of a time-dependent potential),
+// in place; V1 is a pitched plane of the grid's dtype.
+cudaError_t launch_plain_drive(void *re, void *im, const void *v1, bool f64, int nx, int ny,
+                               int64_t pitch, double adt, cudaStream_t st);
 
 // --- observables (reduce.cu) ----------------------------------------------
 // partials: OBS_MAX_BLOCKS * OBS_Q doubles; result: OBS_Q doubles.
@@ -62,8 +66,11 @@ struct FusedLaunch {
     // adjoint support (launch_fused_mid only)
     float *m_re = nullptr, *m_im = nullptr;
     float *g_rh = nullptr, *g_rl = nullptr, *g_ih = nullptr, *g_il = nullptr;
+    // time-dependent potential (launch_fused_drive only): a_n dt of step k
+    float adt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 constexpr int FUSED_MAX_K = 8;
+static_assert(sizeof(FusedLaunch::adt) / sizeof(float) == FUSED_MAX_K, "one a_n dt per step");
 constexpr int FUSED_BOX_COLS = 128;   // columns a warp strip loads (box width)
 constexpr int FUSED_BOX_ROWS = 2;     // rows per pipeline slot (box height)
 cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st);
@@ -71,6 +78,10 @@ cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st);
 // in (m_re, m_im); mode 2 is a backward step (pass the coefficients at
 // -theta) that reads the mid-step state and accumulates G.
 cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st);
+// K (1..4) steps with the time-dependent potential V0 + a_n V1: tm_phase
+// maps three planes (gamma_V, s_V, V1) and adt[k] = a_n dt of step k.
+constexpr int FUSED_DRIVE_MAX_K = 4;
+cudaError_t launch_fused_drive(int K, const FusedLaunch &a, cudaStream_t st);
 
 // Device-resident description of one FP32 grid for the multi-grid launch
 // (written once per grid set-up; read by the kernel with generic loads, its
@@ -102,12 +113,12 @@ int64_t fused_units(int K, int nx, int ny);
 cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, int64_t total_units,
                                int flip, int *err, cudaStream_t st);
 
-// Build a 3-D FP32 tensor map over two consecutive pitched planes (nx x ny
-// each, `plane_bytes` apart) for the fused path: one box load fetches the
-// same rows of both planes.  Returns false (and a message) if the driver
-// entry point is unavailable or the encode call fails.
+// Build a 3-D FP32 tensor map over `planes` (2 or 3) consecutive pitched
+// planes (nx x ny each, `plane_bytes` apart) for the fused path: one box
+// load fetches the same rows of every plane.  Returns false (and a message)
+// if the driver entry point is unavailable or the encode call fails.
 bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
-                          size_t plane_bytes, const char **why);
+                          size_t plane_bytes, const char **why, int planes = 2);
 
 // Thread-local count of kernel launches issued by this library.
 void count_launches(int64_t n);

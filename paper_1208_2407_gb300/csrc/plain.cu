@@ -269,6 +269,23 @@ __global__ void plain_phase_kernel(T *__restrict__ re, T *__restrict__ im,
     }
 }
 
+template <typename T>
+__global__ void plain_drive_kernel(T *__restrict__ re, T *__restrict__ im,
+                                   const T *__restrict__ v1, int nx, int ny, int64_t pitch, T adt)
+{
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        int64_t o = (int64_t)y * pitch;
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx;
+             x += gridDim.x * blockDim.x) {
+            T r = re[o + x], m = im[o + x], g, s;
+            angle_versine(adt * v1[o + x], g, s);
+            phase1(r, m, g, s);
+            re[o + x] = r;
+            im[o + x] = m;
+        }
+    }
+}
+
 inline dim3 grid2d(int64_t per_row, int rows)
 {
     int gx = (int)((per_row + kThreads - 1) / kThreads);
@@ -366,6 +383,18 @@ cudaError_t launch_plain_sweep(void *re, void *im, bool f64, int nx, int ny, int
         else
             plain_sweep_y_kernel<float><<<grid, kThreads, 0, st>>>((float *)re, (float *)im, nx, ny, pitch, parity, (float)g, (float)s);
     }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_drive(void *re, void *im, const void *v1, bool f64, int nx, int ny,
+                               int64_t pitch, double adt, cudaStream_t st)
+{
+    dim3 grid = grid2d(nx, ny);
+    if (f64)
+        plain_drive_kernel<double><<<grid, kThreads, 0, st>>>((double *)re, (double *)im, (const double *)v1, nx, ny, pitch, adt);
+    else
+        plain_drive_kernel<float><<<grid, kThreads, 0, st>>>((float *)re, (float *)im, (const float *)v1, nx, ny, pitch, (float)adt);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -87,6 +87,8 @@ _SIGNATURES = {
     "ts_get_state": [_VP, _VP, _VP, _INT, _INT, _VP],
     "ts_set_potential": [_VP, _VP, _INT, _DBL, _DBL, _VP],
     "ts_set_potential_order": [_VP, _VP, _INT, _DBL, _DBL, _INT, _VP],
+    "ts_set_drive": [_VP, _VP, _INT, _VP, _I64, _VP],
+    "ts_clear_drive": [_VP],
     "ts_evolve": [_VP, _I64, _INT, _VP],
     "ts_evolve_plain": [_VP, _I64, _VP],
     "ts_observe": [_VP, ctypes.POINTER(ts_observables), _VP],
@@ -193,6 +195,14 @@ def ts_evolve(h, steps, K, stream):
 
 def ts_set_potential_order(h, v_ptr, where, dt, theta, order, stream):
     _call("ts_set_potential_order", h, v_ptr, where, dt, theta, order, stream)
+
+
+def ts_set_drive(h, v1_ptr, where, a_ptr, n_a, stream):
+    _call("ts_set_drive", h, v1_ptr, where, a_ptr, n_a, stream)
+
+
+def ts_clear_drive(h):
+    _call("ts_clear_drive", h)
 
 
 def ts_evolve_plain(h, steps, stream):
@@ -386,6 +396,30 @@ class Grid:
         if Va.shape != self.shape:
             raise ValueError("V must have the grid's shape")
         ts_set_potential_order(self.handle, _VP(Va.ctypes.data), TS_HOST, *args)
+
+    def set_drive(self, V1, a, stream=None):
+        """Time-dependent potential V0 + a[n] V1 for the next len(a) steps
+        (V0, dt, theta from set_potential, which must come first)."""
+        st = stream or current_stream_ptr()
+        av = np.ascontiguousarray(np.ravel(a), dtype=np.float64)
+        ap = _VP(av.ctypes.data)
+        if V1 is None:
+            ts_set_drive(self.handle, None, TS_HOST, ap, av.size, st)
+            return
+        torch = _torch()
+        if isinstance(V1, torch.Tensor):
+            if V1.dtype != torch.float64 or tuple(V1.shape) != self.shape or not V1.is_contiguous():
+                raise ValueError("V1 must be a contiguous float64 tensor of the grid's shape")
+            where = TS_DEVICE if V1.is_cuda else TS_HOST
+            ts_set_drive(self.handle, _VP(V1.data_ptr()), where, ap, av.size, st)
+            return
+        V1a = np.ascontiguousarray(V1, dtype=np.float64)
+        if V1a.shape != self.shape:
+            raise ValueError("V1 must have the grid's shape")
+        ts_set_drive(self.handle, _VP(V1a.ctypes.data), TS_HOST, ap, av.size, st)
+
+    def clear_drive(self):
+        ts_clear_drive(self.handle)
 
     def evolve(self, steps: int, K: int = 0, stream=None):
         ts_evolve(self.handle, int(steps), int(K), stream or current_stream_ptr())
