@@ -146,7 +146,7 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
  * with TS_ERR_ARG, before launching anything, if they are asked for more
  * steps than amplitudes are left.  The drive phase exp(-i a[n] dt V1) is
  * computed on the device per site and step (no table); the fused path runs
- * at depth <= 4.  Needs three more planes of ts_layout.plane_bytes,
+ * at depth <= 4 (K = 0: 4).  Needs three more planes of ts_layout.plane_bytes,
  * cudaMalloc'd by the library on first use and freed by ts_destroy_grid.
  * ts_observe's e_pot is sum V0 |psi|^2 (without the drive term).  Driven
  * grids are evolved one by one by ts_evolve_batched and refused by the

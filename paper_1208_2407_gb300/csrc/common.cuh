@@ -45,26 +45,58 @@ __device__ __forceinline__ void phase1(T &r, T &m, T g, T s)
 }
 
 // Versine coefficients of an angle phi computed on the device in FP32:
-// g = 1 - cos phi = 2 sin^2 h, s = sin phi = 2 sin h cos h with h = phi/2.
-// For |h| <= 0.4, sin h and cos h come from their Taylor series through h^7
-// and h^8 (truncation below 2e-9 relative, under half an FP32 ulp); larger
-// angles call sincosf.  g and s share sin h and cos h, so
-// (1 - g)^2 + s^2 - 1 = -4 sin^2 h (1 - sin^2 h - cos^2 h) stays at
-// O(ulp * phi^2): the unitarity defect shrinks with the angle.
+// g = 1 - cos phi = 2 sin^2 h and s = sin phi = 2 sin h cos h, h = phi / 2.
+// Both are unchanged when h moves by a multiple of pi (sin h and cos h change
+// sign together), so h is reduced to r = h - k pi, |r| <= pi/2, by a
+// Cody-Waite split of pi into three floats (the first two have 12 significant
+// bits, so k times them is exact for |k| < 2^12; beyond that the reduction
+// error stays below the rounding error of phi itself).  sin r and cos r come
+// from their Taylor series through r^13 and r^14 (truncation below 7e-10);
+// for |h| <= 0.4 no reduction is needed and the series stop at r^7 and r^8
+// (truncation below 2e-9 relative).  g and s share sin r and cos r, so the
+// unitarity defect (1 - g)^2 + s^2 - 1 = -4 sin^2 r (1 - sin^2 r - cos^2 r)
+// is O(ulp * phi^2) for small angles.
+__device__ __forceinline__ void versine_short(float h, float &g, float &s)
+{
+    const float t = h * h;
+    const float sh = h * fmaf(t, fmaf(t, fmaf(t, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+    const float ch = fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f),
+                             -0.5f), 1.0f);
+    g = 2.0f * sh * sh;
+    s = 2.0f * sh * ch;
+}
+
+__device__ __forceinline__ void versine_reduced(float h, float &g, float &s)
+{
+    const float k = rintf(h * 0.318309886f);             // 1/pi
+    float r = fmaf(-k, 3.140625f, h);                      // pi = A + B + C
+    r = fmaf(-k, 0x1.fb4p-11f, r);
+    r = fmaf(-k, 0x1.4442d2p-23f, r);
+    const float t = r * r;
+    float ps = fmaf(t, -1.0f / 6227020800.0f, 1.0f / 39916800.0f);
+    ps = fmaf(t, ps, -1.0f / 362880.0f);
+    ps = fmaf(t, ps, 1.0f / 5040.0f);
+    ps = fmaf(t, ps, -1.0f / 120.0f);
+    ps = fmaf(t, ps, 1.0f / 6.0f);
+    const float sh = fmaf(-r * t, ps, r);                 // r - r^3/6 + ...
+    float pc = fmaf(t, -1.0f / 87178291200.0f, 1.0f / 479001600.0f);
+    pc = fmaf(t, pc, -1.0f / 3628800.0f);
+    pc = fmaf(t, pc, 1.0f / 40320.0f);
+    pc = fmaf(t, pc, -1.0f / 720.0f);
+    pc = fmaf(t, pc, 1.0f / 24.0f);
+    pc = fmaf(t, pc, -0.5f);
+    const float ch = fmaf(t, pc, 1.0f);
+    g = 2.0f * sh * sh;
+    s = 2.0f * sh * ch;
+}
+
 __device__ __forceinline__ void angle_versine(float phi, float &g, float &s)
 {
     const float h = 0.5f * phi;
-    float sh, ch;
-    if (fabsf(h) <= 0.4f) {
-        const float h2 = h * h;
-        sh = h * fmaf(h2, fmaf(h2, fmaf(h2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
-        ch = fmaf(h2, fmaf(h2, fmaf(h2, fmaf(h2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f),
-                           -0.5f), 1.0f);
-    } else {
-        sincosf(h, &sh, &ch);
-    }
-    g = 2.0f * sh * sh;
-    s = 2.0f * sh * ch;
+    if (fabsf(h) <= 0.4f)
+        versine_short(h, g, s);
+    else
+        versine_reduced(h, g, s);
 }
 
 // The same in FP64 (plain path of FP64 grids).

@@ -141,8 +141,8 @@ struct KParams {
     // double-float planes (g_rh + g_rl, g_ih + g_il)
     float *m_re, *m_im;
     float *g_rh, *g_rl, *g_ih, *g_il;
-    // MODE 3 (time-dependent potential V0 + a(t) V1): a_n dt of step k of
-    // the launch; the phase ring carries V1 as a third plane
+    // MODE 3 (time-dependent potential V0 + a(t) V1): a_n dt / 2 of step k
+    // of the launch; the phase ring carries V1 as a third plane
     float adt[FUSED_MAX_K];
 };
 
@@ -340,14 +340,50 @@ __device__ __forceinline__ void phase4(Frag &f, float4 g, float4 s)
 
 // Drive phase exp(-i a dt V1) of one row of the lane (time-dependent
 // potential): adt = a_n dt of the step, v1 = the row's V1 values.
-template <bool PACKED>
-__device__ __forceinline__ void drive4(Frag &f, float4 v1, float adt)
+// versine_short on two columns at once (same operations, same rounding)
+__device__ __forceinline__ void versine_short2(float2 h, float2 &g, float2 &s)
 {
+    auto c2 = [](float v) { return make_float2(v, v); };
+    const float2 t = __fmul2_rn(h, h);
+    float2 ps = __ffma2_rn(t, c2(-1.0f / 5040.0f), c2(1.0f / 120.0f));
+    ps = __ffma2_rn(t, ps, c2(-1.0f / 6.0f));
+    ps = __ffma2_rn(t, ps, c2(1.0f));
+    const float2 sh = __fmul2_rn(h, ps);
+    float2 pc = __ffma2_rn(t, c2(1.0f / 40320.0f), c2(-1.0f / 720.0f));
+    pc = __ffma2_rn(t, pc, c2(1.0f / 24.0f));
+    pc = __ffma2_rn(t, pc, c2(-0.5f));
+    const float2 ch = __ffma2_rn(t, pc, c2(1.0f));
+    const float2 sh2 = __fmul2_rn(c2(2.0f), sh);
+    g = __fmul2_rn(sh2, sh);
+    s = __fmul2_rn(sh2, ch);
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void drive4(Frag &f, float4 v1, float hdt)
+{
+    // hdt = a_n dt / 2: the half angles of the lane's four columns; one
+    // branch per lane picks the short series when all four are small
+    const float4 h = make_float4(hdt * v1.x, hdt * v1.y, hdt * v1.z, hdt * v1.w);
     float4 g, s;
-    angle_versine(adt * v1.x, g.x, s.x);
-    angle_versine(adt * v1.y, g.y, s.y);
-    angle_versine(adt * v1.z, g.z, s.z);
-    angle_versine(adt * v1.w, g.w, s.w);
+    if (fmaxf(fmaxf(fabsf(h.x), fabsf(h.y)), fmaxf(fabsf(h.z), fabsf(h.w))) <= 0.4f) {
+        if constexpr (PACKED) {
+            float2 g0, s0, g1, s1;
+            versine_short2(lo2(h), g0, s0);
+            versine_short2(hi2(h), g1, s1);
+            g = join2(g0, g1);
+            s = join2(s0, s1);
+        } else {
+            versine_short(h.x, g.x, s.x);
+            versine_short(h.y, g.y, s.y);
+            versine_short(h.z, g.z, s.z);
+            versine_short(h.w, g.w, s.w);
+        }
+    } else {
+        versine_reduced(h.x, g.x, s.x);
+        versine_reduced(h.y, g.y, s.y);
+        versine_reduced(h.z, g.z, s.z);
+        versine_reduced(h.w, g.w, s.w);
+    }
     phase4<PACKED>(f, g, s);
 }
 
@@ -900,7 +936,7 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.g_rl = a.g_rl;
     p.g_ih = a.g_ih;
     p.g_il = a.g_il;
-    for (int k = 0; k < FUSED_MAX_K; ++k) p.adt[k] = a.adt[k];
+    for (int k = 0; k < FUSED_MAX_K; ++k) p.adt[k] = 0.5f * a.adt[k];   // half angles
     const int blocks = (p.total_warps + C::WPC - 1) / C::WPC;
     fused_kernel<K, MODE><<<blocks, C::WPC * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
     count_launches(1);

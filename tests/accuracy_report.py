@@ -132,6 +132,29 @@ def order4_2048():
                  "oracle_site_steps_per_s_nthr": n / tn, "host_cores": NCPU})
 
 
+def driven_2048():
+    c = wl.harmonic_2048(seed=2)
+    n, dt, steps = c["nx"], c["dt"], c["steps"]
+    V1 = (np.arange(n) - n / 2.0)[None, :] * np.ones((n, 1))
+    a = 2e-3 * np.cos(0.05 * (np.arange(steps) + 0.5) * dt)
+    (ore, oim), tn = timed(lambda: oracle.evolve_driven(c["re"], c["im"], c["V"], V1, a, dt,
+                                                        c["theta"], nthreads=NCPU))
+    g = trotter.Grid(n, n, "f32")
+    g.set_state(c["re"], c["im"])
+    g.set_potential(c["V"], dt, c["theta"])
+    g.set_drive(V1, a)
+    o0 = g.observe()
+    ms = gpu_ms(lambda: g.evolve(steps))
+    oT = g.observe()
+    gre, gim = g.get_state(np.float64)
+    g.close()
+    return emit({"workload": "2048^2 harmonic + field along x, a = 2e-3 cos(0.05 t), 1000 steps",
+                 "seed": 2, "fp32_rel_l2": rel_l2(gre, gim, ore, oim),
+                 "fp32_norm_drift": abs(oT["norm"] - o0["norm"]),
+                 "gpu_fp32_site_steps_per_s": n * n * steps / (ms / 1e3),
+                 "oracle_site_steps_per_s_nthr": n * n * steps / tn, "host_cores": NCPU})
+
+
 def roofline_sizes():
     import torch
     rows = []
@@ -229,6 +252,7 @@ def main():
     out = {"c1": plain_fp64_256(),
            "c2": [harmonic_2048(s, s == 0) for s in range(5)],
            "order4": order4_2048(),
+           "drive": driven_2048(),
            "c3": roofline_sizes(),
            "c5": adjoint_1024()}
     c2 = out["c2"]
