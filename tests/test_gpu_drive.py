@@ -75,8 +75,9 @@ def test_fp32_fused_matches_oracle(nx, ny, K):
 
 
 def test_fp32_plain_and_large_angles():
-    """FP32 plain path; and drive angles beyond the series range (|a V1 dt|
-    up to 3), where the kernel calls sincosf."""
+    """FP32 plain path; and drive angles beyond the short series' range
+    (|a V1 dt| up to 3), where the kernel first reduces the angle by a
+    multiple of pi."""
     rng = np.random.default_rng(12)
     re, im, V0, V1, a = drive_inputs(rng, 200, 90, 9)
     gre, gim = run_driven(re, im, V0, V1, a, 0.05, 0.025, path="plain")
@@ -197,3 +198,23 @@ def test_uniform_force_drift_closed_form_on_the_gpu():
         epsabs=1e-13, epsrel=1e-13)
     m = oracle.moments(gre, gim)
     assert abs(m[1] / m[0] - (x0 + drift)) < 2e-3
+
+
+@pytest.mark.parametrize("scale", [1e-3, 1.0, 40.0, 3000.0])
+def test_drive_phase_alone_against_closed_form(scale):
+    """theta = 0 and V0 = 0 leave only the drive phases: psi_T = psi_0
+    exp(-i dt V1 sum_n a_n) per site.  Angles from 1e-5 to ~1e4 rad per step
+    cover the short series and the reduced path; the per-site error bound is
+    about 1e-6 per step (series, reduction and the phase update in FP32)."""
+    rng = np.random.default_rng(16)
+    nx, ny, steps, dt = 160, 40, 8, 0.05
+    re, im = random_state(rng, nx, ny)
+    V1 = rng.uniform(-1.0, 1.0, (ny, nx)) * scale
+    a = rng.uniform(0.5, 1.5, steps)
+    for path in ("fused", "plain"):
+        gre, gim = run_driven(re, im, None, V1, a, dt, 0.0, path=path)
+        expect = (re + 1j * im) * np.exp(-1j * dt * V1 * np.sum(a))
+        err = np.abs((gre + 1j * gim) - expect) / np.maximum(np.abs(re + 1j * im), 1e-30)
+        # FP32 V1 and a_n dt carry a relative rounding of ~1e-7 into the angle
+        bound = 1e-5 + 2.4e-7 * dt * np.abs(V1) * np.sum(a)
+        assert np.all(err < bound), (path, float(np.max(err / bound)))
