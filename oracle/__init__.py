@@ -55,6 +55,12 @@ def bind(lib):
         "oracle_evolve_driven": [_I64, _I64, _DP, _DP, _DP, _DP, _DP, ctypes.c_double,
                                  ctypes.c_double, _I64, ctypes.c_int],
         "oracle_moments": [_I64, _I64, _DP, _DP, _DP],
+        "oracle_sweep3": [_I64, _I64, _I64, _DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                          ctypes.c_int],
+        "oracle_evolve3": [_I64, _I64, _I64, _DP, _DP, _DP, ctypes.c_double, ctypes.c_double,
+                           _I64, ctypes.c_int],
+        "oracle_moments3": [_I64, _I64, _I64, _DP, _DP, _DP],
+        "oracle_energy3": [_I64, _I64, _I64, _DP, _DP, _DP, ctypes.c_double, _DP],
         "oracle_energy": [_I64, _I64, _DP, _DP, _DP, ctypes.c_double, _DP],
         "oracle_inner": [_I64, _DP, _DP, _DP, _DP, _DP],
         "oracle_adjoint_grad": [_I64, _I64, _DP, _DP, _DP, _DP, _DP, ctypes.c_double,
@@ -65,10 +71,11 @@ def bind(lib):
     }
     for name, args in sig.items():
         getattr(lib, name).argtypes = args
-    for name in ("oracle_evolve", "oracle_evolve_driven", "oracle_adjoint_grad"):
+    for name in ("oracle_evolve", "oracle_evolve_driven", "oracle_evolve3", "oracle_adjoint_grad"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("oracle_sweep_x", "oracle_sweep_y", "oracle_phase", "oracle_step2",
                  "oracle_moments", "oracle_energy", "oracle_inner", "oracle_apply_A",
+                 "oracle_sweep3", "oracle_moments3", "oracle_energy3",
                  "oracle_apply_B"):
         getattr(lib, name).restype = None
     lib.oracle_compensated_sum.restype = ctypes.c_double
@@ -152,6 +159,59 @@ def evolve_driven(re, im, V0, V1, a, dt: float, theta: float, nthreads: int = 1)
     if rc != 0:
         raise ValueError("oracle_evolve_driven rejected its arguments (rc=%d)" % rc)
     return re, im
+
+
+def _state3(re, im):
+    re = np.array(re, dtype=np.float64, order="C", copy=True)
+    im = np.array(im, dtype=np.float64, order="C", copy=True)
+    if re.shape != im.shape or re.ndim != 3:
+        raise ValueError("re and im must be 3-D arrays of equal shape (nz, ny, nx)")
+    return re, im
+
+
+def sweep3(re, im, axis: int, parity: int, theta: float, nthreads: int = 1):
+    """One 3-D sweep along axis 0 (x), 1 (y) or 2 (z); arrays (nz, ny, nx)."""
+    lib = _load()
+    re, im = _state3(re, im)
+    nz, ny, nx = re.shape
+    lib.oracle_sweep3(nx, ny, nz, _ptr(re), _ptr(im), int(axis), int(parity), float(theta),
+                      int(nthreads))
+    return re, im
+
+
+def evolve3(re, im, V, dt: float, theta: float, steps: int, nthreads: int = 1):
+    """``steps`` second-order steps on the 3-D lattice; arrays (nz, ny, nx)."""
+    lib = _load()
+    re, im = _state3(re, im)
+    nz, ny, nx = re.shape
+    Vc = None if V is None else _f64(V)
+    if Vc is not None and Vc.shape != re.shape:
+        raise ValueError("V must have the state's shape")
+    rc = lib.oracle_evolve3(nx, ny, nz, _ptr(re), _ptr(im), _ptr(Vc), float(dt), float(theta),
+                            int(steps), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_evolve3 rejected its arguments (rc=%d)" % rc)
+    return re, im
+
+
+def moments3(re, im):
+    """(sum|psi|^2, sum x.., sum y.., sum z.., sum x^2.., sum y^2.., sum z^2..)."""
+    lib = _load()
+    re, im = _f64(re), _f64(im)
+    nz, ny, nx = re.shape
+    out = np.zeros(7)
+    lib.oracle_moments3(nx, ny, nz, _ptr(re), _ptr(im), _ptr(out))
+    return out
+
+
+def energy3(re, im, V, J: float = 1.0):
+    lib = _load()
+    re, im = _f64(re), _f64(im)
+    nz, ny, nx = re.shape
+    Vc = None if V is None else _f64(V)
+    out = np.zeros(2)
+    lib.oracle_energy3(nx, ny, nz, _ptr(re), _ptr(im), _ptr(Vc), float(J), _ptr(out))
+    return float(out[0]), float(out[1])
 
 
 def moments(re, im):

@@ -259,6 +259,89 @@ int oracle_evolve_driven(int64_t nx, int64_t ny, double *re, double *im,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Three dimensions (Sec. 2 splits H into the diagonal and two terms per     */
+/* dimension; Sec. 6 names three-dimensional systems as the next step).      */
+/* Site (x, y, z) is at index (z*ny + y)*nx + x.  One second-order step      */
+/* applies X-even, X-odd, Y-even, Y-odd, Z-even, Z-odd, the phase, then the  */
+/* mirror order, each kinetic factor at the half angle theta.                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t nx, ny, nz;
+    double *re, *im;
+    int parity;
+    double c, s;
+} sweep3_ctx;
+
+/* axis x: rows r = z*ny + y in [lo, hi) */
+static void sweep3_x(void *vctx, int64_t lo, int64_t hi)
+{
+    sweep3_ctx *q = (sweep3_ctx *)vctx;
+    for (int64_t r = lo; r < hi; ++r)
+        for (int64_t x = q->parity; x + 1 < q->nx; x += 2)
+            rotate_pair(q->re, q->im, r * q->nx + x, r * q->nx + x + 1, q->c, q->s);
+}
+
+/* axis y: slabs z in [lo, hi), pairs (y, y+1) inside each slab */
+static void sweep3_y(void *vctx, int64_t lo, int64_t hi)
+{
+    sweep3_ctx *q = (sweep3_ctx *)vctx;
+    for (int64_t z = lo; z < hi; ++z)
+        for (int64_t y = q->parity; y + 1 < q->ny; y += 2)
+            for (int64_t x = 0; x < q->nx; ++x) {
+                int64_t j = (z * q->ny + y) * q->nx + x;
+                rotate_pair(q->re, q->im, j, j + q->nx, q->c, q->s);
+            }
+}
+
+/* axis z: pairs (z, z+1) with z = parity + 2p for p in [lo, hi) */
+static void sweep3_z(void *vctx, int64_t lo, int64_t hi)
+{
+    sweep3_ctx *q = (sweep3_ctx *)vctx;
+    const int64_t plane = q->nx * q->ny;
+    for (int64_t p = lo; p < hi; ++p) {
+        int64_t z = q->parity + 2 * p;
+        if (z + 1 >= q->nz) continue;
+        for (int64_t i = 0; i < plane; ++i)
+            rotate_pair(q->re, q->im, z * plane + i, (z + 1) * plane + i, q->c, q->s);
+    }
+}
+
+/* One sweep along axis 0 (x), 1 (y) or 2 (z) of the given parity. */
+void oracle_sweep3(int64_t nx, int64_t ny, int64_t nz, double *re, double *im, int axis,
+                   int parity, double theta, int nthreads)
+{
+    sweep3_ctx q = {nx, ny, nz, re, im, parity & 1, cos(theta), sin(theta)};
+    if (axis == 0) {
+        parallel_range(ny * nz, nthreads, sweep3_x, &q);
+    } else if (axis == 1) {
+        parallel_range(nz, nthreads, sweep3_y, &q);
+    } else {
+        int64_t npairs = (nz - (parity & 1)) / 2;
+        if (npairs > 0) parallel_range(npairs, nthreads, sweep3_z, &q);
+    }
+}
+
+void oracle_step3(int64_t nx, int64_t ny, int64_t nz, double *re, double *im,
+                  const double *V, double dt, double theta, int nthreads)
+{
+    for (int axis = 0; axis < 3; ++axis)
+        for (int parity = 0; parity < 2; ++parity)
+            oracle_sweep3(nx, ny, nz, re, im, axis, parity, theta, nthreads);
+    oracle_phase(nx, ny * nz, re, im, V, dt, nthreads);
+    for (int axis = 2; axis >= 0; --axis)
+        for (int parity = 1; parity >= 0; --parity)
+            oracle_sweep3(nx, ny, nz, re, im, axis, parity, theta, nthreads);
+}
+
+int oracle_evolve3(int64_t nx, int64_t ny, int64_t nz, double *re, double *im,
+                   const double *V, double dt, double theta, int64_t steps, int nthreads)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || steps < 0 || !re || !im) return -1;
+    for (int64_t n = 0; n < steps; ++n) oracle_step3(nx, ny, nz, re, im, V, dt, theta, nthreads);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Observables (Sec. 2: the norm <psi|psi> is conserved by the unitary U).    */
 /* All sums use Neumaier's compensated summation.                            */
 /* ------------------------------------------------------------------------ */
@@ -315,6 +398,51 @@ void oracle_energy(int64_t nx, int64_t ny, const double *re, const double *im,
             }
             if (V) nsum_add(&pot, V[i] * (re[i] * re[i] + im[i] * im[i]));
         }
+    out[0] = nsum_val(&kin);
+    out[1] = nsum_val(&pot);
+}
+
+/* Three-dimensional moments: (sum |psi|^2, sum x|psi|^2, sum y|psi|^2,
+ * sum z|psi|^2, sum x^2|psi|^2, sum y^2|psi|^2, sum z^2|psi|^2). */
+void oracle_moments3(int64_t nx, int64_t ny, int64_t nz, const double *re,
+                     const double *im, double *out)
+{
+    nsum a[7];
+    memset(a, 0, sizeof(a));
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                int64_t i = (z * ny + y) * nx + x;
+                double p = re[i] * re[i] + im[i] * im[i];
+                nsum_add(&a[0], p);
+                nsum_add(&a[1], (double)x * p);
+                nsum_add(&a[2], (double)y * p);
+                nsum_add(&a[3], (double)z * p);
+                nsum_add(&a[4], (double)x * (double)x * p);
+                nsum_add(&a[5], (double)y * (double)y * p);
+                nsum_add(&a[6], (double)z * (double)z * p);
+            }
+    for (int q = 0; q < 7; ++q) out[q] = nsum_val(&a[q]);
+}
+
+/* <psi|H|psi> on the 3-D lattice: bonds along x, y and z. */
+void oracle_energy3(int64_t nx, int64_t ny, int64_t nz, const double *re, const double *im,
+                    const double *V, double J, double *out)
+{
+    nsum kin = {0, 0}, pot = {0, 0};
+    const int64_t plane = nx * ny;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                int64_t i = (z * ny + y) * nx + x;
+                if (x + 1 < nx)
+                    nsum_add(&kin, -2.0 * J * (re[i] * re[i + 1] + im[i] * im[i + 1]));
+                if (y + 1 < ny)
+                    nsum_add(&kin, -2.0 * J * (re[i] * re[i + nx] + im[i] * im[i + nx]));
+                if (z + 1 < nz)
+                    nsum_add(&kin, -2.0 * J * (re[i] * re[i + plane] + im[i] * im[i + plane]));
+                if (V) nsum_add(&pot, V[i] * (re[i] * re[i] + im[i] * im[i]));
+            }
     out[0] = nsum_val(&kin);
     out[1] = nsum_val(&pot);
 }

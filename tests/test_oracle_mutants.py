@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 
+import test_oracle_3d as three
 import test_oracle_drive as drive
 import test_oracle_pins as pins
 
@@ -47,6 +48,10 @@ MUTANTS = [
      "            Vn[i] = (V0 ? V0[i] : 0.0) + a[0] * (V1 ? V1[i] : 0.0);"),
     ("drive_sign", "            Vn[i] = (V0 ? V0[i] : 0.0) + a[s] * (V1 ? V1[i] : 0.0);",
      "            Vn[i] = (V0 ? V0[i] : 0.0) - a[s] * (V1 ? V1[i] : 0.0);"),
+    ("z_sweeps_missing_from_mirror", "    for (int axis = 2; axis >= 0; --axis)",
+     "    for (int axis = 1; axis >= 0; --axis)"),
+    ("z_pair_one_row_apart", "            rotate_pair(q->re, q->im, z * plane + i, (z + 1) * plane + i, q->c, q->s);",
+     "            if (z * plane + i + q->nx < q->nx * q->ny * q->nz) rotate_pair(q->re, q->im, z * plane + i, z * plane + i + q->nx, q->c, q->s);"),
     ("uncompensated_sum", "    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;\n    else a->c += (v - t) + a->s;\n",
      ""),
 ]
@@ -65,6 +70,7 @@ PIN_CHECKS = [
     pins.test_compensated_sum_is_exactly_rounded_on_cancellation,
     lambda: pins.test_adjoint_matches_finite_differences(6, 5, 12),
     drive.test_driven_steps_equal_dense_products,
+    lambda: [three.test_step_equals_dense_product(*d) for d in [(2, 2, 2), (2, 3, 4)]],
     drive.test_uniform_drive_is_a_global_phase,
 ]
 
