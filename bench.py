@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--n3", type=int, default=512, help="side of the 3-D lattice in --variants")
     ap.add_argument("--variants", action="store_true",
                     help="time fourth-order steps and a time-dependent potential instead "
                          "(prints its own JSON line)")
@@ -543,9 +544,11 @@ def paper_sizes(args):
 def method_variants(args):
     """The method's variants on the n x n random-Gaussian workload, inputs
     resident in HBM: second order (the default depth), fourth-order steps U4
-    (five second-order substeps; counted per U4 step) at a few depths, and a
+    (five second-order substeps; counted per U4 step) at a few depths, a
     time-dependent potential V0 + a(t) V1 (a field along x oscillating in
-    time; the drive phase is computed per site and step on the device)."""
+    time; the drive phase is computed per site and step on the device), and
+    an n3^3 lattice (harmonic V, a Gaussian packet) on the fast and the plain
+    3-D paths."""
     import torch
     from paper_1208_2407_gb300 import trotter
     from paper_1208_2407_gb300 import workloads as wl
@@ -588,6 +591,47 @@ def method_variants(args):
                      "site_substeps_per_s": float(n) * n * substeps / (t / 1e3),
                      "norm": g.norm()})
     g.close()
+    del re0, im0, Vd, V1
+    torch.cuda.empty_cache()
+    # a 3-D lattice: n3^3 sites, separable packet and harmonic V built on the device
+    n3 = args.n3
+    t = torch.arange(n3, dtype=torch.float64, device="cuda")
+    env = torch.exp(-((t - n3 / 2.0) ** 2) / (4.0 * (n3 / 16.0) ** 2))
+    g1 = env * torch.exp(0.5j * t)
+    g1 = g1 / torch.sqrt(torch.sum(torch.abs(g1) ** 2))
+    psi = torch.einsum("z,y,x->zyx", g1, g1, g1)
+    re3 = psi.real.float().contiguous()
+    im3 = psi.imag.float().contiguous()
+    del psi
+    r2 = (t - n3 / 2.0) ** 2
+    V3 = (0.5e-4 * (r2[None, None, :] + r2[None, :, None] + r2[:, None, None])).contiguous()
+    g3 = trotter.Grid(n3, n3, "f32", nz=n3)
+    T3 = max(1, T // 4)
+    for path in ("fused", "plain"):
+        steps = T3 if path == "fused" else max(1, T3 // 10)
+        ms = []
+        for rep in range(max(1, args.steps) + 1):
+            g3.set_state(re3, im3)
+            g3.set_potential(V3, c["dt"], c["theta"])
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            trotter.ts_launch_count(reset=True)
+            a.record()
+            if path == "fused":
+                g3.evolve(steps)
+            else:
+                g3.evolve_plain(steps)
+            b.record()
+            torch.cuda.synchronize()
+            if rep > 0:
+                ms.append(a.elapsed_time(b))
+        tm = float(np.median(ms))
+        runs.append({"variant": "3-D %d^3 %s" % (n3, path), "order": 2, "K": 1, "steps": steps,
+                     "ms": tm, "launches": trotter.ts_launch_count(),
+                     "site_steps_per_s": float(n3) ** 3 * steps / (tm / 1e3),
+                     "site_substeps_per_s": float(n3) ** 3 * steps / (tm / 1e3),
+                     "norm": g3.norm()})
+    g3.close()
     print(json.dumps({"metric": "site-steps/s of the method's variants", "n": n, "runs": runs,
                       "data": "synthetic", "inputs": "resident in HBM"}), flush=True)
     return 0

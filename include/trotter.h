@@ -60,16 +60,35 @@ typedef struct ts_grid ts_grid;
  *   pitch        row pitch of every plane, in elements (multiple of 32)
  *   plane_bytes  bytes per plane (multiple of 256)
  *   slab_bytes   total bytes: 7 planes (re, im, ping-pong re, im, the two
- *                potential-phase tables, V) plus reduction scratch. */
+ *                potential-phase tables, V) plus reduction scratch
+ *   nz           slabs of a 3-D grid (1 for a 2-D grid); slab z holds rows
+ *                z*ny .. z*ny + ny - 1 of every plane. */
 typedef struct {
     int64_t nx, ny, pitch;
     size_t plane_bytes, slab_bytes;
     ts_dtype dtype;
+    int64_t nz;
 } ts_layout;
 
 /* Compute the layout of an nx x ny grid of `dtype` without allocating.
  * Errors: TS_ERR_ARG if nx or ny < 1, nx or ny > 2^20, or out == NULL. */
 ts_status ts_grid_layout(int64_t nx, int64_t ny, ts_dtype dtype, ts_layout *out);
+
+/* Three-dimensional lattices (Sec. 2's splitting with two hopping terms per
+ * dimension, extended to z as Sec. 6 proposes).  Site (x, y, z) of a dense
+ * array is at (z*ny + y)*nx + x; every call that takes or returns dense
+ * arrays (state, V) then uses nx*ny*nz elements.  One step applies X-even,
+ * X-odd, Y-even, Y-odd, Z-even, Z-odd, exp(-i V dt), then the mirror order.
+ * ts_evolve runs, for FP32 grids with even ny < 2^16 and |theta| <= pi/4,
+ * a streaming Z pass and the fused 2-D step (depth 1, Y pairs kept inside
+ * each slab) in turn: n steps take 2n + 1 passes over HBM (K is ignored);
+ * otherwise, and for ts_evolve_plain, one kernel per sweep.  ts_observe adds
+ * <z>, <z^2> and the z bonds.  3-D grids take order 2 only, no drive, no
+ * adjoint, and ts_evolve_batched evolves them one by one.  Errors: as for
+ * 2-D, and TS_ERR_ARG if ny * nz > 2^30. */
+ts_status ts_grid_layout3(int64_t nx, int64_t ny, int64_t nz, ts_dtype dtype, ts_layout *out);
+ts_status ts_create_grid3(int64_t nx, int64_t ny, int64_t nz, ts_dtype dtype, void *slab,
+                          size_t slab_bytes, ts_grid **out);
 
 /* Create a grid handle.  `slab` is a device pointer of at least
  * ts_grid_layout().slab_bytes bytes, 256-byte aligned, owned by the caller
@@ -185,6 +204,7 @@ typedef struct {
     double x2, y2;      /* <x^2>, <y^2>                                      */
     double e_kin;       /* -J sum over neighbour pairs 2 Re(conj(psi_j) psi_k) */
     double e_pot;       /* sum V |psi|^2                                     */
+    double z, z2;       /* <z>, <z^2> (3-D grids; 0 for 2-D grids)           */
 } ts_observables;
 
 ts_status ts_observe(ts_grid *g, ts_observables *out, void *stream);

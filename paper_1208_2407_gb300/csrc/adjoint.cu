@@ -120,9 +120,9 @@ ts_status ts_adjoint_forward(ts_grid *g, const void *target_re, const void *targ
     if (!g || !target_re || !target_im || !ws || !fidelity)
         return err(TS_ERR_ARG, "ts_adjoint_forward: null argument");
     if (g->f64()) return err(TS_ERR_UNSUPPORTED, "ts_adjoint_forward: FP32 grids only");
-    if (g->order != 2 || g->driven)
+    if (g->order != 2 || g->driven || g->is3d())
         return err(TS_ERR_UNSUPPORTED,
-                   "ts_adjoint_forward: second-order grids with a static potential only");
+                   "ts_adjoint_forward: second-order 2-D grids with a static potential only");
     if (std::fabs(g->theta) > 0.25 * M_PI)
         return err(TS_ERR_UNSUPPORTED, "ts_adjoint_forward: |theta| must be <= pi/4");
     if (steps < 1 || ckpt_every < 1)

@@ -49,8 +49,8 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 size_t scratch_bytes()
 {
     // partials, result, error word, multi-grid descriptor
-    return round_up(sizeof(double) * ts::OBS_MAX_BLOCKS * ts::OBS_Q, 256) +
-           round_up(sizeof(double) * ts::OBS_Q, 256) + 256 +
+    return round_up(sizeof(double) * ts::OBS_MAX_BLOCKS * ts::OBS_Q3, 256) +
+           round_up(sizeof(double) * ts::OBS_Q3, 256) + 256 +
            round_up(sizeof(ts::GridDesc), 256);
 }
 
@@ -69,9 +69,9 @@ ts_status grid_setup(const ts_layout &L, void *slab, bool owns_slab, ts_grid **o
     g->slab = (unsigned char *)slab;
     unsigned char *scr = g->slab + kPlanes * L.plane_bytes;
     g->partials = (double *)scr;
-    scr += round_up(sizeof(double) * OBS_MAX_BLOCKS * OBS_Q, 256);
+    scr += round_up(sizeof(double) * OBS_MAX_BLOCKS * OBS_Q3, 256);
     g->result = (double *)scr;
-    scr += round_up(sizeof(double) * OBS_Q, 256);
+    scr += round_up(sizeof(double) * OBS_Q3, 256);
     g->err = (int *)scr;
     scr += 256;
     g->desc_dev = (GridDesc *)scr;
@@ -89,9 +89,9 @@ ts_status grid_setup(const ts_layout &L, void *slab, bool owns_slab, ts_grid **o
         const char *why = "";
         bool ok = true;
         for (int c = 0; c < 2 && ok; ++c)
-            ok = make_pair_tensor_map(&g->tm_state[c], g->plane(2 * c), (int)L.nx, (int)L.ny,
+            ok = make_pair_tensor_map(&g->tm_state[c], g->plane(2 * c), (int)L.nx, (int)g->rows(),
                                       L.pitch, L.plane_bytes, &why);
-        ok = ok && make_pair_tensor_map(&g->tm_phase, g->pg(), (int)L.nx, (int)L.ny, L.pitch,
+        ok = ok && make_pair_tensor_map(&g->tm_phase, g->pg(), (int)L.nx, (int)g->rows(), L.pitch,
                                         L.plane_bytes, &why);
         if (!ok) {
             delete g;
@@ -229,31 +229,47 @@ int64_t ts_launch_count(int reset)
     return v;
 }
 
-ts_status ts_grid_layout(int64_t nx, int64_t ny, ts_dtype dtype, ts_layout *out)
+ts_status ts_grid_layout3(int64_t nx, int64_t ny, int64_t nz, ts_dtype dtype, ts_layout *out)
 {
     if (!out) return fail(TS_ERR_ARG, "ts_grid_layout: out is NULL");
-    if (nx < 1 || ny < 1 || nx > kMaxSide || ny > kMaxSide)
-        return fail(TS_ERR_ARG, "ts_grid_layout: sides must be in [1, 2^20], got %lld x %lld",
-                    (long long)nx, (long long)ny);
+    if (nx < 1 || ny < 1 || nz < 1 || nx > kMaxSide || ny > kMaxSide || nz > kMaxSide)
+        return fail(TS_ERR_ARG,
+                    "ts_grid_layout: sides must be in [1, 2^20], got %lld x %lld x %lld",
+                    (long long)nx, (long long)ny, (long long)nz);
+    if (ny * nz > (int64_t(1) << 30))
+        return fail(TS_ERR_ARG, "ts_grid_layout: ny * nz must be at most 2^30, got %lld",
+                    (long long)(ny * nz));
     if (dtype != TS_F32 && dtype != TS_F64)
         return fail(TS_ERR_ARG, "ts_grid_layout: unknown dtype %d", (int)dtype);
     const size_t es = dtype == TS_F64 ? 8 : 4;
     out->nx = nx;
     out->ny = ny;
     out->pitch = (int64_t)round_up((size_t)nx, 32);
-    out->plane_bytes = round_up((size_t)out->pitch * (size_t)ny * es, 256);
+    out->plane_bytes = round_up((size_t)out->pitch * (size_t)ny * (size_t)nz * es, 256);
     out->slab_bytes = kPlanes * out->plane_bytes + scratch_bytes();
     out->dtype = dtype;
+    out->nz = nz;
     return TS_OK;
+}
+
+ts_status ts_grid_layout(int64_t nx, int64_t ny, ts_dtype dtype, ts_layout *out)
+{
+    return ts_grid_layout3(nx, ny, 1, dtype, out);
 }
 
 ts_status ts_create_grid(int64_t nx, int64_t ny, ts_dtype dtype, void *slab, size_t slab_bytes,
                          ts_grid **out)
 {
+    return ts_create_grid3(nx, ny, 1, dtype, slab, slab_bytes, out);
+}
+
+ts_status ts_create_grid3(int64_t nx, int64_t ny, int64_t nz, ts_dtype dtype, void *slab,
+                          size_t slab_bytes, ts_grid **out)
+{
     if (!out) return fail(TS_ERR_ARG, "ts_create_grid: out is NULL");
     *out = nullptr;
     ts_layout L;
-    ts_status st = ts_grid_layout(nx, ny, dtype, &L);
+    ts_status st = ts_grid_layout3(nx, ny, nz, dtype, &L);
     if (st != TS_OK) return st;
     if (slab) {
         if (((uintptr_t)slab & 255u) != 0)
@@ -321,7 +337,7 @@ namespace {
 // planes, contiguous in the slab) and convert it into `dst` on the device.
 ts_status stage_in(ts_grid *g, const void *host, ts_dtype src_dtype, void *dst, cudaStream_t st)
 {
-    const size_t n = (size_t)g->L.nx * (size_t)g->L.ny;
+    const size_t n = (size_t)g->L.nx * (size_t)g->rows();
     const size_t es = src_dtype == TS_F64 ? 8 : 4;
     if (n * es > 2 * g->L.plane_bytes)
         return fail(TS_ERR_ARG, "staging region too small");  // cannot happen by layout
@@ -329,7 +345,7 @@ ts_status stage_in(ts_grid *g, const void *host, ts_dtype src_dtype, void *dst, 
     cudaError_t e = cudaMemcpyAsync(stage, host, n * es, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     e = ts::launch_convert_in(stage, src_dtype == TS_F64, dst, g->f64(), (int)g->L.nx,
-                              (int)g->L.ny, g->L.pitch, st);
+                              (int)g->rows(), g->L.pitch, st);
     if (e != cudaSuccess) return cuda_fail(e, "convert kernel");
     return TS_OK;
 }
@@ -360,7 +376,7 @@ ts_status ts_set_state(ts_grid *g, const void *re, const void *im, ts_dtype src_
         return fail(TS_ERR_ARG, "ts_set_state: unknown dtype");
     cudaStream_t st = (cudaStream_t)stream;
     const bool sf = src_dtype == TS_F64;
-    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    const int nx = (int)g->L.nx, ny = (int)g->rows();   // rows: all slabs
     if (where == TS_DEVICE) {
         cudaError_t e = ts::launch_convert_in(re, sf, g->re(), g->f64(), nx, ny, g->L.pitch, st);
         if (e == cudaSuccess)
@@ -402,7 +418,7 @@ ts_status ts_get_state(ts_grid *g, void *re, void *im, ts_dtype dst_dtype, ts_me
     ts_status s = check_errword(g, st);
     if (s != TS_OK) return s;
     const bool df = dst_dtype == TS_F64;
-    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    const int nx = (int)g->L.nx, ny = (int)g->rows();   // rows: all slabs
     const size_t n = (size_t)nx * ny;
     cudaError_t e;
     if (where == TS_DEVICE) {
@@ -456,10 +472,12 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
         return fail(TS_ERR_ARG, "ts_set_potential: unknown memory kind");
     if (order != 2 && order != 4)
         return fail(TS_ERR_ARG, "ts_set_potential_order: order must be 2 or 4, got %d", order);
+    if (order == 4 && g->is3d())
+        return fail(TS_ERR_UNSUPPORTED, "ts_set_potential_order: order 4 on 2-D grids only");
     cudaStream_t st = (cudaStream_t)stream;
     g->driven = false;   // a new potential ends any time-dependent drive
     g->drive_a.clear();
-    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    const int nx = (int)g->L.nx, ny = (int)g->rows();   // rows: all slabs
     cudaError_t e;
     // fourth order (Eq. fourthorder): U4(dt) = U2(p dt)^2 U2((1-4p) dt) U2(p dt)^2
     // with p = 1 / (4 - 4^(1/3)); substep a = p dt uses planes 4/5, substep
@@ -518,11 +536,12 @@ ts_status ts_set_drive(ts_grid *g, const double *V1, ts_mem where, const double 
     if (n_a < 0 || (n_a > 0 && !a)) return fail(TS_ERR_ARG, "ts_set_drive: bad amplitude array");
     if (where != TS_HOST && where != TS_DEVICE)
         return fail(TS_ERR_ARG, "ts_set_drive: unknown memory kind");
-    if (g->order != 2) return fail(TS_ERR_UNSUPPORTED, "ts_set_drive: second-order grids only");
+    if (g->order != 2 || g->is3d())
+        return fail(TS_ERR_UNSUPPORTED, "ts_set_drive: second-order 2-D grids only");
     for (int64_t i = 0; i < n_a; ++i)
         if (!std::isfinite(a[i])) return fail(TS_ERR_ARG, "ts_set_drive: a[%lld] is not finite", (long long)i);
     cudaStream_t st = (cudaStream_t)stream;
-    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    const int nx = (int)g->L.nx, ny = (int)g->rows();   // rows: all slabs
     const size_t PB = g->L.plane_bytes;
     cudaError_t e;
     if (!g->drive_slab) {
@@ -581,7 +600,7 @@ namespace {
 ts_status plain_run(ts_grid *g, int64_t steps, const ts::RotCoef &c, const void *pg,
                     const void *ps, cudaStream_t st, const double *drive_adt = nullptr)
 {
-    const int nx = (int)g->L.nx, ny = (int)g->L.ny;
+    const int nx = (int)g->L.nx, ny = (int)g->rows();   // rows: all slabs
     const int64_t pitch = g->L.pitch;
     void *re = g->re(), *im = g->im();
     const bool f = g->f64();
@@ -590,17 +609,25 @@ ts_status plain_run(ts_grid *g, int64_t steps, const ts::RotCoef &c, const void 
         gg = (double)(float)gg;
         ss = (double)(float)ss;
     }
+    // one sweep: X over all rows; Y inside each slab and Z between slabs on
+    // 3-D grids (X-even, X-odd, Y-even, Y-odd[, Z-even, Z-odd], phase, mirror)
+    const int sy = (int)g->L.ny, sz = (int)g->L.nz;
+    auto sweep = [&](int axis, int parity) {
+        if (axis == 0 || !g->is3d())
+            return ts::launch_plain_sweep(re, im, f, nx, ny, pitch, axis, parity, gg, ss, st);
+        if (axis == 1)
+            return ts::launch_plain_sweep_y3(re, im, f, nx, sy, sz, pitch, parity, gg, ss, st);
+        return ts::launch_plain_sweep_z(re, im, f, nx, sy, sz, pitch, parity, gg, ss, st);
+    };
+    const int n_fam = g->is3d() ? 6 : 4;
     for (int64_t n = 0; n < steps; ++n) {
         cudaError_t e = cudaSuccess;
-        const int seq_axis[4] = {0, 0, 1, 1}, seq_par[4] = {0, 1, 0, 1};
-        for (int i = 0; i < 4 && e == cudaSuccess; ++i)
-            e = ts::launch_plain_sweep(re, im, f, nx, ny, pitch, seq_axis[i], seq_par[i], gg, ss, st);
+        for (int i = 0; i < n_fam && e == cudaSuccess; ++i) e = sweep(i / 2, i & 1);
         if (e == cudaSuccess)
             e = ts::launch_plain_phase(re, im, pg, ps, f, nx, ny, pitch, st);
         if (e == cudaSuccess && drive_adt)
             e = ts::launch_plain_drive(re, im, g->drive_v1(), f, nx, ny, pitch, drive_adt[n], st);
-        for (int i = 3; i >= 0 && e == cudaSuccess; --i)
-            e = ts::launch_plain_sweep(re, im, f, nx, ny, pitch, seq_axis[i], seq_par[i], gg, ss, st);
+        for (int i = n_fam - 1; i >= 0 && e == cudaSuccess; --i) e = sweep(i / 2, i & 1);
         if (e != cudaSuccess) return cuda_fail(e, "plain sweep launch");
     }
     return TS_OK;
@@ -623,7 +650,8 @@ ts_status fused_run(ts_grid *g, int64_t steps, int K, const ts::RotCoef &c,
         a.out_re = (float *)g->re_other();
         a.out_im = (float *)g->im_other();
         a.nx = (int)g->L.nx;
-        a.ny = (int)g->L.ny;
+        a.ny = (int)g->rows();
+        a.ny_slab = g->is3d() ? (int)g->L.ny : 0;
         a.pitch = g->L.pitch;
         a.t1 = (float)c.t1;
         a.s1 = (float)c.s1;
@@ -662,6 +690,36 @@ ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
 // neighbouring steps run back to back (a run of 2 at either end, of 4
 // between two b substeps), so on the fused path each run of r substeps is
 // ceil(r / K) launches of near-equal depth; each b substep is one launch.
+// 3-D steps on the fast path (FP32, |theta| <= pi/4, even ny, ny < 2^16).
+// Z factors commute with X and Y factors, so the step
+//   Xe Xo Ye Yo Ze Zo P Zo Ze Yo Ye Xo Xe
+// equals Ze Zo [Xe Xo Ye Yo P Yo Ye Xo Xe] Zo Ze: a Z pass, the 2-D step
+// with Y pairs kept inside slabs (fused kernel at depth 1), a Z pass.  The Z
+// halves of neighbouring steps merge, Zo Ze Ze Zo = Zo Ze(2 theta) Zo, so n
+// steps take n + 1 Z passes (each one streaming pass over HBM).
+ts_status evolve3_fused(ts_grid *g, int64_t steps, cudaStream_t st)
+{
+    const int nx = (int)g->L.nx, ny = (int)g->L.ny, nz = (int)g->L.nz;
+    const float t1 = (float)g->t1, s1 = (float)g->s1, t2 = (float)g->t2, s2 = (float)g->s2;
+    const ts::ZSeq first = {2, {0, 1, 0}, {t1, t1, 0.f}, {s1, s1, 0.f}};
+    const ts::ZSeq mid = {3, {1, 0, 1}, {t1, t2, t1}, {s1, s2, s1}};
+    const ts::ZSeq last = {2, {1, 0, 0}, {t1, t1, 0.f}, {s1, s1, 0.f}};
+    auto zpass = [&](const ts::ZSeq &q) -> ts_status {
+        cudaError_t e = ts::launch_zstream((const float *)g->re(), (const float *)g->im(),
+                                           (float *)g->re_other(), (float *)g->im_other(), nx, ny,
+                                           nz, g->L.pitch, q, st);
+        if (e != cudaSuccess) return cuda_fail(e, "z-stream kernel launch");
+        g->cur ^= 1;
+        return TS_OK;
+    };
+    ts_status s = zpass(first);
+    for (int64_t n = 0; n < steps && s == TS_OK; ++n) {
+        s = fused_run(g, 1, 1, grid_coef(g), &g->tm_phase, st);
+        if (s == TS_OK) s = zpass(n + 1 < steps ? mid : last);
+    }
+    return s;
+}
+
 // Steps with the time-dependent potential V0 + a_n V1: the next `steps`
 // amplitudes, each multiplied by dt; the fused kernel at depth <= 4 or,
 // for FP64 grids and |theta| > pi/4, the plain path.
@@ -724,6 +782,11 @@ ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     if (g->f64() && K != 0)
         return fail(TS_ERR_UNSUPPORTED, "ts_evolve: FP64 grids run the plain path (K must be 0)");
+    if (g->is3d()) {
+        if (g->f64() || std::fabs(g->theta) > 0.25 * M_PI || (g->L.ny & 1) || g->L.ny > 65535)
+            return plain_steps(g, steps, st);
+        return evolve3_fused(g, steps, st);
+    }
     if (g->driven)
         return evolve_driven(g, steps, K, g->f64() || std::fabs(g->theta) > 0.25 * M_PI, st);
     if (g->order == 4) {
@@ -757,14 +820,14 @@ ts_status ts_evolve_batched(ts_grid *const *gs, int n, const int64_t *steps, int
     if (K < 0 || K > ts::FUSED_MAX_K) return fail(TS_ERR_ARG, "ts_evolve_batched: K must be in [0, 8]");
     cudaStream_t st = (cudaStream_t)stream;
     const int depth = K == 0 ? auto_depth() : K;
-    // grids the multi-grid kernel can take: FP32, second order, no drive,
-    // |theta| <= pi/4; the rest evolve one by one
+    // grids the multi-grid kernel can take: 2-D, FP32, second order, no
+    // drive, |theta| <= pi/4; the rest evolve one by one
     std::vector<ts_grid *> multi;
     std::vector<int64_t> msteps;
     for (int i = 0; i < n; ++i) {
         if (!gs[i] || steps[i] < 0) return fail(TS_ERR_ARG, "ts_evolve_batched: grid %d", i);
         if (steps[i] == 0) continue;
-        if (gs[i]->f64() || gs[i]->order != 2 || gs[i]->driven ||
+        if (gs[i]->f64() || gs[i]->order != 2 || gs[i]->driven || gs[i]->is3d() ||
             std::fabs(gs[i]->theta) > 0.25 * M_PI) {
             ts_status s = ts_evolve(gs[i], steps[i], K, stream);
             if (s != TS_OK) return s;
@@ -780,13 +843,24 @@ ts_status ts_evolve_batched(ts_grid *const *gs, int n, const int64_t *steps, int
 
 namespace {
 
+// res: OBS_Q3 doubles; 2-D grids fill the first OBS_Q and zero the rest.
 ts_status observe(ts_grid *g, bool norm_only, double *res, cudaStream_t st)
 {
-    cudaError_t e = ts::launch_observe(g->re(), g->im(), g->vp(), g->f64(), (int)g->L.nx,
-                                       (int)g->L.ny, g->L.pitch, g->J, norm_only, g->partials,
-                                       g->result, st);
+    cudaError_t e;
+    int nq = ts::OBS_Q;
+    for (int q = 0; q < ts::OBS_Q3; ++q) res[q] = 0.0;
+    if (g->is3d() && !norm_only) {
+        e = ts::launch_observe3(g->re(), g->im(), g->vp(), g->f64(), (int)g->L.nx, (int)g->L.ny,
+                                (int)g->L.nz, g->L.pitch, g->J, g->partials, g->result, st);
+        nq = ts::OBS_Q3;
+    } else {
+        // the norm needs no geometry: a 3-D grid is ny*nz rows of sites
+        e = ts::launch_observe(g->re(), g->im(), g->vp(), g->f64(), (int)g->L.nx,
+                               (int)g->rows(), g->L.pitch, g->J, norm_only, g->partials,
+                               g->result, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "observables kernel");
-    e = cudaMemcpyAsync(res, g->result, sizeof(double) * ts::OBS_Q, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(res, g->result, sizeof(double) * nq, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e, "observables copy");
     return check_errword(g, st);
 }
@@ -796,7 +870,7 @@ ts_status observe(ts_grid *g, bool norm_only, double *res, cudaStream_t st)
 ts_status ts_observe(ts_grid *g, ts_observables *out, void *stream)
 {
     if (!g || !out) return fail(TS_ERR_ARG, "ts_observe: null argument");
-    double r[ts::OBS_Q];
+    double r[ts::OBS_Q3];
     ts_status s = observe(g, false, r, (cudaStream_t)stream);
     if (s != TS_OK) return s;
     out->norm = r[0];
@@ -807,13 +881,15 @@ ts_status ts_observe(ts_grid *g, ts_observables *out, void *stream)
     out->y2 = r[4] * inv;
     out->e_kin = r[5];
     out->e_pot = r[6];
+    out->z = r[7] * inv;
+    out->z2 = r[8] * inv;
     return TS_OK;
 }
 
 ts_status ts_norm(ts_grid *g, double *out, void *stream)
 {
     if (!g || !out) return fail(TS_ERR_ARG, "ts_norm: null argument");
-    double r[ts::OBS_Q];
+    double r[ts::OBS_Q3];
     ts_status s = observe(g, true, r, (cudaStream_t)stream);
     if (s != TS_OK) return s;
     *out = r[0];

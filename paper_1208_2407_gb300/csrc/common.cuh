@@ -33,6 +33,21 @@ __device__ __forceinline__ void rot2(T &ar, T &ai, T &br, T &bi, T g, T s)
     rot1(br, bi, ar0, ai0, g, s);
 }
 
+// Both members of a pair in lifting form: the rotation a' = c a + i s b,
+// b' = i s a + c b is two real plane rotations, of (a_re, b_im) and of
+// (b_re, a_im), each applied as three shears x -= t y; y += s x; x -= t y
+// with t = tan(theta/2), s = sin(theta) (6 FMA per pair, determinant 1).
+__device__ __forceinline__ void rot_lift(float &ar, float &ai, float &br, float &bi, float t,
+                                         float s)
+{
+    ar = fmaf(-t, bi, ar);
+    br = fmaf(-t, ai, br);
+    bi = fmaf(s, ar, bi);
+    ai = fmaf(s, br, ai);
+    ar = fmaf(-t, bi, ar);
+    br = fmaf(-t, ai, br);
+}
+
 // psi <- psi * exp(-i phi) with g = 1 - cos(phi), s = sin(phi):
 //   (r + i m)((1 - g) - i s) = (r - g r + s m) + i (m - g m - s r)
 template <typename T>

@@ -133,6 +133,8 @@ struct KParams {
     int64_t units;
     int total_warps;
     int strip_warps;         // > 0: warps per strip of the strip-aligned split
+    int ny_slab;             // > 0: a 3-D grid of ny / ny_slab slabs; no Y pair
+                             // crosses a slab boundary (ny_slab even)
     float t1, s1, g1, t2, s2;
     int *err;
     // adjoint support (K = 1 only): MODE 1 writes the mid-step state m (after
@@ -228,17 +230,6 @@ __device__ __forceinline__ void tma_load_pair(void *dst, const CUtensorMap *tm, 
 // 6 FMA per pair instead of 8; every shear has determinant 1.  A lane that
 // holds one member of a pair (the pair straddling two lanes) updates only
 // that member, in the versine form a' = a - g a + i s b (4 FMA).
-__device__ __forceinline__ void rot_lift(float &ar, float &ai, float &br, float &bi, float t,
-                                         float s)
-{
-    ar = fmaf(-t, bi, ar);
-    br = fmaf(-t, ai, br);
-    bi = fmaf(s, ar, bi);
-    ai = fmaf(s, br, ai);
-    ar = fmaf(-t, bi, ar);
-    br = fmaf(-t, ai, br);
-}
-
 struct XEven {
     float t0, s0, t1, s1;   // pairs (c0,c1) and (c2,c3) of the lane's float4, lifting form
 };
@@ -484,7 +475,10 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
     static_assert(MODE == 0 || MODE == 3 || K == 1, "mid-step modes exist for K = 1 only");
     using C = Cfg<K, MODE == 3>;
     constexpr int NSP = C::NSP;
-    auto yok = [&](int y) { return INTERIOR || (y >= 0 && y + 1 < p.ny); };
+    auto yok = [&](int y) {
+        return INTERIOR ||
+               (y >= 0 && y + 1 < p.ny && (p.ny_slab == 0 || (y + 1) % p.ny_slab != 0));
+    };
     auto slot_p = [&](int back) -> const unsigned char * {   // phase slot j - back
         int q = pos_p - back;
         if (q < 0) q += NSP;
@@ -768,7 +762,8 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     for (int i = 0; i < 2 * K; ++i) cA[i] = zero_frag();
     auto interior = [&](int j) {
         const int yin = s.Ys + 2 * j;
-        return j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny;
+        return j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny &&
+               (p.ny_slab == 0 || (yin - 2 * K) / p.ny_slab == (yin + 1) / p.ny_slab);
     };
     for (int j = 0; j < s.n_iter;) {
         if (j + 1 < s.n_iter && interior(j) && interior(j + 1)) {
@@ -870,6 +865,7 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
         p.err = err;
         p.n_pairs = (p.ny + 1) / 2;
         p.strip_warps = 0;
+        p.ny_slab = 0;
         const int64_t local = u - e.unit_begin;
         const int64_t g_units = (gi + 1 < n_grids ? tab[gi + 1].unit_begin : total_units) -
                                 e.unit_begin;
@@ -924,6 +920,7 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
         p.strip_warps = (int)w;
         p.total_warps = (int)(w * p.n_strips);
     }
+    p.ny_slab = a.ny_slab;
     p.t1 = a.t1;
     p.s1 = a.s1;
     p.g1 = a.g1;

@@ -62,6 +62,9 @@ struct ts_grid {
     void *pg_b() const { return tab_b; }
     void *ps_b() const { return tab_b + L.plane_bytes; }
     bool f64() const { return L.dtype == TS_F64; }
+    // rows of every plane: ny per slab, nz slabs (3-D grids; nz = 1 in 2-D)
+    int64_t rows() const { return L.ny * L.nz; }
+    bool is3d() const { return L.nz > 1; }
 };
 
 

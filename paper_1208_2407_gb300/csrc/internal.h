@@ -16,6 +16,7 @@ enum : int { ERRBIT_WAIT_TIMEOUT = 1, ERRBIT_BAD_CONFIG = 2 };
 
 // Number of FP64 quantities the observables reduction produces per block.
 constexpr int OBS_Q = 7;
+constexpr int OBS_Q3 = 9;   // 3-D grids: the 7 quantities plus sum z p and sum z^2 p
 constexpr int OBS_MAX_BLOCKS = 1024;
 
 // --- conversions, tables, plain path (plain.cu) ---------------------------
@@ -39,12 +40,43 @@ cudaError_t launch_plain_phase(void *re, void *im, const void *pg, const void *p
 cudaError_t launch_plain_drive(void *re, void *im, const void *v1, bool f64, int nx, int ny,
                                int64_t pitch, double adt, cudaStream_t st);
 
+// --- three-dimensional lattices (lattice3d.cu) ----------------------------
+// A 3-D grid of nx x ny x nz sites keeps slab z (rows z*ny .. z*ny + ny - 1
+// of every plane) right after slab z - 1, so the 2-D kernels see a grid of
+// ny*nz rows.  X sweeps, the phase and the tables need nothing else.
+// One Y sweep inside every slab (pairs (y, y+1), y of the given parity
+// counted from the slab's first row), in place.
+cudaError_t launch_plain_sweep_y3(void *re, void *im, bool f64, int nx, int ny, int nz,
+                                  int64_t pitch, int parity, double g, double s,
+                                  cudaStream_t st);
+// One Z sweep: pairs of slabs (z, z+1), z of the given parity, in place.
+cudaError_t launch_plain_sweep_z(void *re, void *im, bool f64, int nx, int ny, int nz,
+                                 int64_t pitch, int parity, double g, double s, cudaStream_t st);
+// Up to three Z sweeps applied in one streaming pass over an FP32 grid,
+// from the planes (in_re, in_im) to (out_re, out_im): sweep i pairs slabs
+// (z, z+1) with z % 2 == parity[i], in lifting form (t[i], s[i]).
+struct ZSeq {
+    int m;
+    int parity[3];
+    float t[3], s[3];
+};
+cudaError_t launch_zstream(const float *in_re, const float *in_im, float *out_re, float *out_im,
+                           int nx, int ny, int nz, int64_t pitch, const ZSeq &q,
+                           cudaStream_t st);
+
 // --- observables (reduce.cu) ----------------------------------------------
 // partials: OBS_MAX_BLOCKS * OBS_Q doubles; result: OBS_Q doubles.
 // norm_only computes only sum |psi|^2 (result[0]).
 cudaError_t launch_observe(const void *re, const void *im, const void *vplane, bool f64,
                            int nx, int ny, int64_t pitch, double J, bool norm_only,
                            double *partials, double *result, cudaStream_t st);
+
+// The same for a 3-D grid: OBS_Q3 quantities (sum p, sum x p, sum y p,
+// sum x^2 p, sum y^2 p, kinetic, potential, sum z p, sum z^2 p), bonds along
+// x, y (inside slabs) and z; partials hold OBS_MAX_BLOCKS * OBS_Q3 doubles.
+cudaError_t launch_observe3(const void *re, const void *im, const void *vplane, bool f64,
+                            int nx, int ny, int nz, int64_t pitch, double J, double *partials,
+                            double *result, cudaStream_t st);
 
 // <phi|psi> = sum conj(phi) psi over two FP32 pitched states: result[0] real,
 // result[1] imaginary part (exact products, double-float then FP64 sums).
@@ -68,6 +100,9 @@ struct FusedLaunch {
     float *g_rh = nullptr, *g_rl = nullptr, *g_ih = nullptr, *g_il = nullptr;
     // time-dependent potential (launch_fused_drive only): a_n dt of step k
     float adt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // 3-D grids: rows per slab (ny above counts all rows, slab by slab);
+    // 0 for 2-D grids
+    int ny_slab = 0;
 };
 constexpr int FUSED_MAX_K = 8;
 static_assert(sizeof(FusedLaunch::adt) / sizeof(float) == FUSED_MAX_K, "one a_n dt per step");

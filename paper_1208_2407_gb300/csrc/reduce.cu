@@ -290,8 +290,91 @@ observe_kernel(const T *__restrict__ re, const T *__restrict__ im, const T *__re
     }
 }
 
+// Observables of a 3-D grid (slab z = rows z*ny .. z*ny + ny - 1): every
+// term in FP64 (it is called at report points only), runs of 4 sites summed
+// plainly and added into Neumaier-compensated per-thread sums.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-observe_finalize_kernel(const double *__restrict__ partials, int nblocks, int nq,
+observe3_kernel(const T *__restrict__ re, const T *__restrict__ im, const T *__restrict__ vp,
+                int nx, int ny, int nz, int64_t pitch, double J, double *__restrict__ partials)
+{
+    constexpr int NQ = OBS_Q3;
+    Neu acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = {0.0, 0.0};
+    const int64_t rows = (int64_t)ny * nz;
+    const int64_t slab = (int64_t)ny * pitch;
+    const int chunks_per_row = (nx + 3) / 4;
+    const int64_t nchunks = (int64_t)chunks_per_row * rows;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = c / chunks_per_row;
+        const int x0 = (int)(c - r * chunks_per_row) * 4;
+        const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
+        const int64_t o = r * pitch;
+        double run[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) run[q] = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int x = x0 + u;
+            if (x >= nx) break;
+            const double a = (double)re[o + x], b = (double)im[o + x];
+            const double p = a * a + b * b;
+            run[0] += p;
+            run[1] += (double)x * p;
+            run[2] += (double)y * p;
+            run[3] += (double)x * (double)x * p;
+            run[4] += (double)y * (double)y * p;
+            double kin = 0.0;
+            if (x + 1 < nx) kin += a * (double)re[o + x + 1] + b * (double)im[o + x + 1];
+            if (y + 1 < ny) kin += a * (double)re[o + pitch + x] + b * (double)im[o + pitch + x];
+            if (z + 1 < nz) kin += a * (double)re[o + slab + x] + b * (double)im[o + slab + x];
+            run[5] += -2.0 * J * kin;
+            run[6] += (double)vp[o + x] * p;
+            run[7] += (double)z * p;
+            run[8] += (double)z * (double)z * p;
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q].add(run[q]);
+    }
+    __shared__ double sh_s[kThreads / 32][NQ], sh_c[kThreads / 32][NQ];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        Neu a = acc[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            Neu b;
+            b.s = __shfl_down_sync(0xffffffffu, a.s, off);
+            b.c = __shfl_down_sync(0xffffffffu, a.c, off);
+            neu_merge(a, b);
+        }
+        if (lane == 0) {
+            sh_s[warp][q] = a.s;
+            sh_c[warp][q] = a.c;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            Neu a = {0.0, 0.0};
+            if (lane < kThreads / 32) a = {sh_s[lane][q], sh_c[lane][q]};
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                Neu b;
+                b.s = __shfl_down_sync(0xffffffffu, a.s, off);
+                b.c = __shfl_down_sync(0xffffffffu, a.c, off);
+                neu_merge(a, b);
+            }
+            if (lane == 0) partials[(int64_t)blockIdx.x * OBS_Q3 + q] = a.val();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+observe_finalize_kernel(const double *__restrict__ partials, int nblocks, int nq, int stride,
                         double *__restrict__ result)
 {
     __shared__ double sh_s[kThreads / 32], sh_c[kThreads / 32];
@@ -299,7 +382,7 @@ observe_finalize_kernel(const double *__restrict__ partials, int nblocks, int nq
     for (int q = 0; q < nq; ++q) {
         Neu a = {0.0, 0.0};
         for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-            a.add(partials[(int64_t)b * OBS_Q + q]);
+            a.add(partials[(int64_t)b * stride + q]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             Neu o;
@@ -349,7 +432,24 @@ cudaError_t launch_observe(const void *re, const void *im, const void *vplane, b
         else
             observe_f32_kernel<false><<<nblocks, kThreads, 0, st>>>((const float *)re, (const float *)im, (const float *)vplane, nx, ny, pitch, J_hi, J_lo, partials);
     }
-    observe_finalize_kernel<<<1, kThreads, 0, st>>>(partials, nblocks, norm_only ? 1 : OBS_Q, result);
+    observe_finalize_kernel<<<1, kThreads, 0, st>>>(partials, nblocks, norm_only ? 1 : OBS_Q, OBS_Q,
+                                                    result);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observe3(const void *re, const void *im, const void *vplane, bool f64, int nx,
+                            int ny, int nz, int64_t pitch, double J, double *partials,
+                            double *result, cudaStream_t st)
+{
+    const int64_t nchunks = (int64_t)((nx + 3) / 4) * ny * nz;
+    int64_t b = (nchunks + kThreads * 8 - 1) / (kThreads * 8);
+    int nblocks = (int)(b < 1 ? 1 : (b > OBS_MAX_BLOCKS ? OBS_MAX_BLOCKS : b));
+    if (f64)
+        observe3_kernel<double><<<nblocks, kThreads, 0, st>>>((const double *)re, (const double *)im, (const double *)vplane, nx, ny, nz, pitch, J, partials);
+    else
+        observe3_kernel<float><<<nblocks, kThreads, 0, st>>>((const float *)re, (const float *)im, (const float *)vplane, nx, ny, nz, pitch, J, partials);
+    observe_finalize_kernel<<<1, kThreads, 0, st>>>(partials, nblocks, OBS_Q3, OBS_Q3, result);
     count_launches(2);
     return cudaGetLastError();
 }
@@ -363,7 +463,7 @@ cudaError_t launch_inner(const float *phi_re, const float *phi_im, const float *
     int nblocks = (int)(b < 1 ? 1 : (b > OBS_MAX_BLOCKS ? OBS_MAX_BLOCKS : b));
     inner_f32_kernel<<<nblocks, kThreads, 0, st>>>(phi_re, phi_im, psi_re, psi_im, nx, ny, pitch,
                                                    partials);
-    observe_finalize_kernel<<<1, kThreads, 0, st>>>(partials, nblocks, 2, result);
+    observe_finalize_kernel<<<1, kThreads, 0, st>>>(partials, nblocks, 2, OBS_Q, result);
     count_launches(2);
     return cudaGetLastError();
 }

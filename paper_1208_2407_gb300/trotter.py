@@ -38,11 +38,12 @@ class TrotterError(RuntimeError):
 class ts_layout(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("pitch", ctypes.c_int64),
                 ("plane_bytes", ctypes.c_size_t), ("slab_bytes", ctypes.c_size_t),
-                ("dtype", ctypes.c_int)]
+                ("dtype", ctypes.c_int), ("nz", ctypes.c_int64)]
 
 
 class ts_observables(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in ("norm", "x", "y", "x2", "y2", "e_kin", "e_pot")]
+    _fields_ = [(n, ctypes.c_double)
+                for n in ("norm", "x", "y", "x2", "y2", "e_kin", "e_pot", "z", "z2")]
 
 
 class ts_server_cfg(ctypes.Structure):
@@ -81,6 +82,8 @@ _DBL = ctypes.c_double
 _SIGNATURES = {
     "ts_grid_layout": [_I64, _I64, _INT, ctypes.POINTER(ts_layout)],
     "ts_create_grid": [_I64, _I64, _INT, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)],
+    "ts_grid_layout3": [_I64, _I64, _I64, _INT, ctypes.POINTER(ts_layout)],
+    "ts_create_grid3": [_I64, _I64, _I64, _INT, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)],
     "ts_destroy_grid": [_VP],
     "ts_grid_info": [_VP, ctypes.POINTER(ts_layout), ctypes.POINTER(_VP), ctypes.POINTER(_VP)],
     "ts_set_state": [_VP, _VP, _VP, _INT, _INT, _VP],
@@ -170,6 +173,18 @@ def ts_grid_layout(nx: int, ny: int, dtype: int = TS_F32) -> ts_layout:
 def ts_create_grid(nx, ny, dtype, slab_ptr, slab_bytes):
     h = _VP()
     _call("ts_create_grid", nx, ny, dtype, slab_ptr, slab_bytes, ctypes.byref(h))
+    return h
+
+
+def ts_grid_layout3(nx: int, ny: int, nz: int, dtype: int = TS_F32) -> ts_layout:
+    L = ts_layout()
+    _call("ts_grid_layout3", nx, ny, nz, dtype, ctypes.byref(L))
+    return L
+
+
+def ts_create_grid3(nx, ny, nz, dtype, slab_ptr, slab_bytes):
+    h = _VP()
+    _call("ts_create_grid3", nx, ny, nz, dtype, slab_ptr, slab_bytes, ctypes.byref(h))
     return h
 
 
@@ -326,20 +341,21 @@ def _array_ptr(a, shape):
 
 
 class Grid:
-    """One lattice on the current CUDA device, with its slab owned by torch."""
+    """One lattice on the current CUDA device, with its slab owned by torch.
+    nz > 1 makes a 3-D lattice; its arrays have shape (nz, ny, nx)."""
 
-    def __init__(self, nx: int, ny: int, dtype: str = "f32"):
+    def __init__(self, nx: int, ny: int, dtype: str = "f32", nz: int = 1):
         torch = _torch()
-        self.nx, self.ny = int(nx), int(ny)
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.dtype = TS_F64 if dtype in ("f64", "float64", np.float64) else TS_F32
-        self.layout = ts_grid_layout(self.nx, self.ny, self.dtype)
+        self.layout = ts_grid_layout3(self.nx, self.ny, self.nz, self.dtype)
         self.slab = torch.empty(int(self.layout.slab_bytes), dtype=torch.uint8, device="cuda")
-        self.handle = ts_create_grid(self.nx, self.ny, self.dtype, _VP(self.slab.data_ptr()),
-                                     int(self.layout.slab_bytes))
+        self.handle = ts_create_grid3(self.nx, self.ny, self.nz, self.dtype,
+                                      _VP(self.slab.data_ptr()), int(self.layout.slab_bytes))
 
     @property
     def shape(self):
-        return (self.ny, self.nx)
+        return (self.nz, self.ny, self.nx) if self.nz > 1 else (self.ny, self.nx)
 
     def close(self):
         if self.handle is not None:

@@ -32,6 +32,40 @@ def gaussian_packet(nx: int, ny: int, x0: float, y0: float, sigma: float,
     return np.ascontiguousarray(psi.real), np.ascontiguousarray(psi.imag)
 
 
+def gaussian_packet3(nx: int, ny: int, nz: int, x0: float, y0: float, z0: float,
+                     sigma: float, kx: float = 0.0, ky: float = 0.0, kz: float = 0.0):
+    """The 3-D packet, arrays of shape (nz, ny, nx): the product of three 1-D
+    Gaussians with the same sigma, normalised on the grid."""
+    axes = []
+    for n, c, k in ((nx, x0, kx), (ny, y0, ky), (nz, z0, kz)):
+        t = np.arange(n, dtype=np.float64)
+        g = np.exp(-((t - c) ** 2) / (4.0 * sigma * sigma)) * np.exp(1j * k * t)
+        axes.append(g / np.sqrt(np.sum(np.abs(g) ** 2)))
+    psi = np.einsum("z,y,x->zyx", axes[2], axes[1], axes[0])
+    return np.ascontiguousarray(psi.real), np.ascontiguousarray(psi.imag)
+
+
+def harmonic_potential3(nx: int, ny: int, nz: int, w: float):
+    """V = 0.5 w^2 r^2 about the grid centre (nx/2, ny/2, nz/2), shape (nz, ny, nx)."""
+    x = np.arange(nx, dtype=np.float64) - nx / 2.0
+    y = np.arange(ny, dtype=np.float64) - ny / 2.0
+    z = np.arange(nz, dtype=np.float64) - nz / 2.0
+    return 0.5 * w * w * (x[None, None, :] ** 2 + y[None, :, None] ** 2 + z[:, None, None] ** 2)
+
+
+def harmonic_3d(n: int = 128, steps: int = 200, seed: int = 0):
+    """n^3 lattice, harmonic V (w = 1e-2), a packet drawn as in the 2-D case
+    (centre in the middle half of each axis, sigma in [n/16, n/8], momentum
+    components in [-1, 1]); draw order x0, y0, z0, sigma, kx, ky, kz."""
+    rng = np.random.default_rng(seed)
+    x0, y0, z0 = (rng.uniform(n / 4.0, 3.0 * n / 4.0) for _ in range(3))
+    sigma = rng.uniform(n / 16.0, n / 8.0)
+    kx, ky, kz = (rng.uniform(-1.0, 1.0) for _ in range(3))
+    re, im = gaussian_packet3(n, n, n, x0, y0, z0, sigma, kx, ky, kz)
+    V = harmonic_potential3(n, n, n, 1e-2)
+    return dict(nx=n, ny=n, nz=n, re=re, im=im, V=V, dt=DT, theta=THETA, steps=steps, seed=seed)
+
+
 def random_packet_params(rng: np.random.Generator, nx: int, ny: int,
                          sigma_range=(16.0, 64.0)):
     """Draw (x0, y0, sigma, kx, ky), in that order.
