@@ -399,7 +399,10 @@ def run_ours(args):
         g = None
         nbuf = 2
         grids = [trotter.Grid(n, n, "f32") for _ in range(nbuf)]
-        streams = [torch.cuda.Stream() for _ in range(nbuf)]
+        # unequal priorities keep the two grids out of step: the first grid's
+        # kernels go first, and the second grid's copies overlap them (equal
+        # priorities measured 23.8 ms per step against 20.8 ms, kernels 19.3)
+        streams = [torch.cuda.Stream(priority=-1 if i == 0 else 0) for i in range(nbuf)]
         h_re = torch.from_numpy(c["re"].astype(np.float32)).pin_memory()
         h_im = torch.from_numpy(c["im"].astype(np.float32)).pin_memory()
         h_V = torch.from_numpy(c["V"]).pin_memory()
@@ -435,7 +438,8 @@ def run_ours(args):
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(n * n * (4 + 4 + 8)),
                "d2h_bytes_per_step": int(n * n * (4 + 4) + 7 * 8),
-               "pipeline": "%d grids on %d streams, one host thread each" % (nbuf, nbuf),
+               "pipeline": "%d grids on %d streams (high and normal priority), one host "
+                           "thread each" % (nbuf, nbuf),
                "steps": per * nbuf}
         for gg in grids:
             gg.close()
