@@ -140,10 +140,10 @@ ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
  *     p = 1 / (4 - 4^(1/3)),
  * where each substep U2(w dt) uses the kinetic angle w theta and the phase
  * exp(-i V w dt) (w = 1 - 4p is negative: that substep runs backwards).  The
- * grid's phase planes then hold the table at p dt, and a second table at
- * (1-4p) dt (two planes of ts_layout.plane_bytes) is cudaMalloc'd by the
- * library on the first order-4 call and freed by ts_destroy_grid, also for
- * grids on a caller-provided slab.  Fourth-order grids are evolved one by one
+ * grid's phase planes then hold the table at p dt; four more planes of
+ * ts_layout.plane_bytes (the tables at p dt and (1-4p) dt side by side) are
+ * cudaMalloc'd by the library on the first order-4 call and freed by
+ * ts_destroy_grid, also for grids on a caller-provided slab.  Fourth-order grids are evolved one by one
  * by ts_evolve_batched and are refused by the adjoint calls
  * (TS_ERR_UNSUPPORTED).  Errors: TS_ERR_ARG (order not 2 or 4, non-finite dt
  * or theta), TS_ERR_OOM (the second table), TS_ERR_CUDA. */
@@ -185,9 +185,10 @@ ts_status ts_clear_drive(ts_grid *g);
  * depth automatically, 1 <= K <= 8 forces it; a remainder of steps % K runs
  * at a smaller depth).  FP64 grids run the one-sweep-per-kernel path (K
  * must be 0).  On a grid set to order 4 (ts_set_potential_order) each step
- * is U4(dt): the p dt substeps of neighbouring steps run as fused launches
- * of depth at most K (K = 0: 4), each (1-4p) dt substep as a depth-1 launch.
- * Async. */
+ * is U4(dt): with K = 0 each step is one launch that applies all five
+ * substeps; with K >= 1 the p dt substeps of neighbouring steps run as
+ * fused launches of depth at most K and each (1-4p) dt substep as a
+ * depth-1 launch.  Async. */
 ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream);
 
 /* The plain path: one kernel per sweep (8 sweeps + the phase = 9 launches

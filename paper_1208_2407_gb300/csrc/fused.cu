@@ -100,7 +100,12 @@ constexpr uint32_t FULL = 0xffffffffu;
 //    last one K row pairs later, so it needs PF + K + 1 slots.
 // Shallow pipelines (K <= 2) are memory bound and prefetch deeper; deep ones
 // are arithmetic bound and keep shared memory small for occupancy.
-template <int K, bool DRIVE = false>
+// Planes of a phase-ring slot: (gamma_V, s_V); with a drive (MODE 3) also
+// V1; for the fused fourth-order step (MODE 4) the tables of both substep
+// lengths (gamma_a, s_a, gamma_b, s_b).
+__host__ __device__ constexpr int phase_planes(int mode) { return mode == 3 ? 3 : mode == 4 ? 4 : 2; }
+
+template <int K, int PP = 2>
 struct Cfg {
     static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
     static constexpr int PF = K == 1 ? TS_FUSED_PF_K1 : K == 2 ? TS_FUSED_PF_K2 : TS_FUSED_PF_DEEP;
@@ -116,7 +121,7 @@ struct Cfg {
     static constexpr int HALO = ((2 * K + 3) / 4) * 4;
     static constexpr int VALID = FUSED_BOX_COLS - 2 * HALO;
     // a phase slot holds (gamma_V, s_V) and, with a drive, the V1 rows too
-    static constexpr int PSLOT = (DRIVE ? 3 : 2) * PLANE_SLOT_BYTES;
+    static constexpr int PSLOT = PP * PLANE_SLOT_BYTES;
     static constexpr int WARP_SMEM = NSS * SLOT_BYTES + NSP * PSLOT;
     static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + (NSS + NSP) * 8);
 };
@@ -146,6 +151,10 @@ struct KParams {
     // MODE 3 (time-dependent potential V0 + a(t) V1): a_n dt / 2 of step k
     // of the launch; the phase ring carries V1 as a third plane
     float adt[FUSED_MAX_K];
+    // MODE 4 (one fourth-order step U4 = a a b a a, K = 5): t1, s1, g1, t2,
+    // s2 are the a substep's; the b substep's angle (lifting tb, sb; versine
+    // gb) and the merged angle of an a-b boundary (lifting tab, sab)
+    float tb, sb, gb, tab, sab;
 };
 
 // ---- PTX wrappers ---------------------------------------------------------
@@ -398,6 +407,8 @@ __device__ __forceinline__ float4 lds4(const unsigned char *slot, int plane, int
 struct StripCoef {
     XEven E1, E2;   // even pairs at theta and 2 theta
     XOdd O;         // odd pairs at theta
+    XOdd Ob;        // MODE 4: odd pairs at the b substep's angle
+    XEven Eab;      // MODE 4: even pairs at the a + b angle
 };
 
 // Rows and columns this warp owns in its current row range.
@@ -472,8 +483,12 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
                                               const StripCoef &c, const KParams &p, int lane,
                                               const Owned &w, Frag &O0, Frag &O1)
 {
-    static_assert(MODE == 0 || MODE == 3 || K == 1, "mid-step modes exist for K = 1 only");
-    using C = Cfg<K, MODE == 3>;
+    static_assert(MODE == 0 || MODE == 3 || MODE == 4 || K == 1,
+                  "mid-step modes exist for K = 1 only");
+    static_assert(MODE != 4 || K == 5, "the fused fourth-order step has five substeps");
+    using C = Cfg<K, phase_planes(MODE)>;
+    // MODE 4: substep k of U4 = a a b a a is b for k == 2 (angle and table)
+    auto is_b = [](int k) { return MODE == 4 && k == 2; };
     constexpr int NSP = C::NSP;
     auto yok = [&](int y) {
         return INTERIOR ||
@@ -524,40 +539,50 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
     }
 #pragma unroll
     for (int k = 1; k < K; ++k) {
-        {   // Yo (theta), aligned on (y1, y1+1), y1 odd
+        // angles of the two steps that meet here (MODE 4: a or b) and of
+        // their merged factors (2a, or a + b)
+        const bool bp = is_b(k - 1), bk = is_b(k), mixed = bp != bk;
+        const float tp = bp ? p.tb : p.t1, sp_ = bp ? p.sb : p.s1;
+        const float tk = bk ? p.tb : p.t1, sk = bk ? p.sb : p.s1;
+        const float tm = mixed ? p.tab : p.t2, sm = mixed ? p.sab : p.s2;
+        const XOdd &Op = bp ? c.Ob : c.O, &Ok = bk ? c.Ob : c.O;
+        const XEven &Em = mixed ? c.Eab : c.E2;
+        {   // Yo (theta of step k-1), aligned on (y1, y1+1), y1 odd
             const bool v = yok(y1);
-            y_pair<C::PACKED>(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+            y_pair<C::PACKED>(P, Q, v ? tp : 0.f, v ? sp_ : 0.f);
         }
-        // X group between two phases: Xo, Xe(2 theta), Xo
-        x_odd(P, c.O);
-        x_odd(Q, c.O);
-        x_even(P, c.E2);
-        x_even(Q, c.E2);
-        x_odd(P, c.O);
-        x_odd(Q, c.O);
+        // X group between two phases: Xo, Xe(merged), Xo
+        x_odd(P, Op);
+        x_odd(Q, Op);
+        x_even(P, Em);
+        x_even(Q, Em);
+        x_odd(P, Ok);
+        x_odd(Q, Ok);
         Frag P2 = cin[2 * k - 1], Q2 = P;     // rows (y1-1, y1)
-        {   // Ye (2 theta), shifted: pair (y1-1, y1)
+        {   // Ye (merged), shifted: pair (y1-1, y1)
             const bool v = yok(y1 - 1);
-            y_pair<C::PACKED>(P2, Q2, v ? p.t2 : 0.f, v ? p.s2 : 0.f);
+            y_pair<C::PACKED>(P2, Q2, v ? tm : 0.f, v ? sm : 0.f);
         }
         cout[2 * k - 1] = Q;
         P = cin[2 * k];                       // rows (y1-2, y1-1)
-        {   // Yo (theta), shifted: pair (y1-2, y1-1)
+        {   // Yo (theta of step k), shifted: pair (y1-2, y1-1)
             const bool v = yok(y1 - 2);
-            y_pair<C::PACKED>(P, P2, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+            y_pair<C::PACKED>(P, P2, v ? tk : 0.f, v ? sk : 0.f);
         }
         cout[2 * k] = Q2;
         Q = P2;
         y1 -= 2;
         // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
+        // (MODE 4: the b substep reads the slot's second table, planes 2, 3)
+        const int tpl = bk ? 2 : 0;
         if (INTERIOR || j - k - 1 >= 0) {
             const unsigned char *sp = slot_p(k + 1);
-            phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
+            phase4<C::PACKED>(P, lds4(sp, tpl, 1, lane), lds4(sp, tpl + 1, 1, lane));
             if constexpr (MODE == 3) drive4<C::PACKED>(P, lds4(sp, 2, 1, lane), p.adt[k]);
         }
         if (INTERIOR || j - k >= 0) {
             const unsigned char *sp = slot_p(k);
-            phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), lds4(sp, 1, 0, lane));
+            phase4<C::PACKED>(Q, lds4(sp, tpl, 0, lane), lds4(sp, tpl + 1, 0, lane));
             if constexpr (MODE == 3) drive4<C::PACKED>(Q, lds4(sp, 2, 0, lane), p.adt[k]);
         }
     }
@@ -589,10 +614,10 @@ struct WarpRings {
     uint32_t par_s, par_p;
 };
 
-template <int K, bool DRIVE = false>
+template <int K, int PP = 2>
 __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int warp, int lane)
 {
-    using C = Cfg<K, DRIVE>;
+    using C = Cfg<K, PP>;
     constexpr int NSS = C::NSS, NSP = C::NSP;
     WarpRings r;
     // barriers first, then 1 KiB-aligned slots (state ring, phase ring)
@@ -633,10 +658,10 @@ __device__ __forceinline__ void issue_state(WarpRings &r, const Seg &s, int pos,
     tma_load_pair(r.ring_s + pos * SLOT_BYTES, s.tm_state, s.XL, s.Ys + 2 * j, &r.bar_s[pos]);
 }
 
-template <int K, bool DRIVE = false>
+template <int K, int PP = 2>
 __device__ __forceinline__ void issue_phase(WarpRings &r, const Seg &s, int pos, int j)
 {
-    constexpr int PSLOT = Cfg<K, DRIVE>::PSLOT;
+    constexpr int PSLOT = Cfg<K, PP>::PSLOT;
     mbar_expect_tx(&r.bar_p[pos], PSLOT);
     tma_load_pair(r.ring_p + pos * PSLOT, s.tm_phase, s.XL, s.Ys + 2 * j, &r.bar_p[pos]);
 }
@@ -649,7 +674,7 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
                                          const Frag (&cin)[2 * K], Frag (&cout)[2 * K],
                                          int &issued_s, int &issued_p)
 {
-    using C = Cfg<K, MODE == 3>;
+    using C = Cfg<K, phase_planes(MODE)>;
     constexpr int NSS = C::NSS, NSP = C::NSP;
     const int lane = s.lane;
     bool ok = mbar_wait(&r.bar_s[r.pos_s], r.par_s, WAIT_LIMIT_NS) &&
@@ -700,7 +725,7 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
         fence_proxy_async();
         if (more_s) issue_state<K>(r, s, r.pos_s, js);
         if (more_p)
-            issue_phase<K, MODE == 3>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
+            issue_phase<K, phase_planes(MODE)>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
     }
     issued_s += more_s;
     issued_p += more_p;
@@ -717,7 +742,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
                                             const CUtensorMap *tm_phase, const KParams &p,
                                             int sx, int q0, int q1, int lane)
 {
-    using C = Cfg<K, MODE == 3>;
+    using C = Cfg<K, phase_planes(MODE)>;
     constexpr int NSS = C::NSS, NSP = C::NSP, HALO = C::HALO, VALID = C::VALID;
     Seg s;
     s.tm_state = tm_state;
@@ -739,6 +764,11 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     s.c.E2 = {e0 ? p.t2 : 0.f, e0 ? p.s2 : 0.f, e1 ? p.t2 : 0.f, e1 ? p.s2 : 0.f};
     s.c.O = {o0 ? p.t1 : 0.f, o0 ? p.s1 : 0.f, oR ? p.g1 : 0.f,
              oR ? p.s1 : 0.f, oL ? p.g1 : 0.f, oL ? p.s1 : 0.f};
+    if constexpr (MODE == 4) {
+        s.c.Ob = {o0 ? p.tb : 0.f, o0 ? p.sb : 0.f, oR ? p.gb : 0.f,
+                  oR ? p.sb : 0.f, oL ? p.gb : 0.f, oL ? p.sb : 0.f};
+        s.c.Eab = {e0 ? p.tab : 0.f, e0 ? p.sab : 0.f, e1 ? p.tab : 0.f, e1 ? p.sab : 0.f};
+    }
     s.store_lane = lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
     s.own = {s.Y0, s.Y1, xg, s.store_lane};
 
@@ -748,7 +778,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
         fence_proxy_async();
         for (int j = 0; j < n_pro_p; ++j) {
             if (j < n_pro_s) issue_state<K>(r, s, (r.pos_s + j) % NSS, j);
-            issue_phase<K, MODE == 3>(r, s, (r.pos_p + j) % NSP, j);
+            issue_phase<K, phase_planes(MODE)>(r, s, (r.pos_p + j) % NSP, j);
         }
     }
     int issued_s = n_pro_s, issued_p = n_pro_p;
@@ -797,7 +827,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * Cfg<K>::WPC + warp;
     if (gw >= p.total_warps) return;
-    WarpRings r = carve_rings<K, MODE == 3>(smem_raw, warp, lane);
+    WarpRings r = carve_rings<K, phase_planes(MODE)>(smem_raw, warp, lane);
     if (p.strip_warps > 0) {
         // strip-aligned split: warp (sx, i) takes row range i of strip sx, so
         // warps of neighbouring strips walk the same rows at the same time and
@@ -883,7 +913,7 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
 template <int K, int MODE>
 cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
 {
-    using C = Cfg<K, MODE == 3>;
+    using C = Cfg<K, phase_planes(MODE)>;
     static int blocks_per_sm = -1;
     static int num_sms = 0;
     if (blocks_per_sm < 0) {
@@ -934,6 +964,11 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.g_ih = a.g_ih;
     p.g_il = a.g_il;
     for (int k = 0; k < FUSED_MAX_K; ++k) p.adt[k] = 0.5f * a.adt[k];   // half angles
+    p.tb = a.tb;
+    p.sb = a.sb;
+    p.gb = a.gb;
+    p.tab = a.tab;
+    p.sab = a.sab;
     const int blocks = (p.total_warps + C::WPC - 1) / C::WPC;
     fused_kernel<K, MODE><<<blocks, C::WPC * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
     count_launches(1);
@@ -1053,6 +1088,8 @@ cudaError_t launch_fused_drive(int K, const FusedLaunch &a, cudaStream_t st)
     }
 }
 
+cudaError_t launch_fused_u4(const FusedLaunch &a, cudaStream_t st) { return launch_k<5, 4>(a, st); }
+
 cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st)
 {
     if (mode == 1) return launch_k<1, 1>(a, st);
@@ -1075,8 +1112,8 @@ bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int
         }
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    if (planes < 1 || planes > 3) {
-        *why = "tensor map: 1 to 3 planes";
+    if (planes < 1 || planes > 4) {
+        *why = "tensor map: 1 to 4 planes";
         return false;
     }
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};

@@ -103,6 +103,10 @@ struct FusedLaunch {
     // 3-D grids: rows per slab (ny above counts all rows, slab by slab);
     // 0 for 2-D grids
     int ny_slab = 0;
+    // the fused fourth-order step (launch_fused_u4): t1..s2 above are the
+    // a substep's; the b substep's lifting (tb, sb) and versine (gb) forms,
+    // and the merged angle a + b in lifting form (tab, sab)
+    float tb = 0, sb = 0, gb = 0, tab = 0, sab = 0;
 };
 constexpr int FUSED_MAX_K = 8;
 static_assert(sizeof(FusedLaunch::adt) / sizeof(float) == FUSED_MAX_K, "one a_n dt per step");
@@ -117,6 +121,9 @@ cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st);
 // maps three planes (gamma_V, s_V, V1) and adt[k] = a_n dt of step k.
 constexpr int FUSED_DRIVE_MAX_K = 4;
 cudaError_t launch_fused_drive(int K, const FusedLaunch &a, cudaStream_t st);
+// One fourth-order step U4 = a a b a a in one launch (five substeps, depth
+// 5): tm_phase maps four planes (gamma_a, s_a, gamma_b, s_b).
+cudaError_t launch_fused_u4(const FusedLaunch &a, cudaStream_t st);
 
 // Device-resident description of one FP32 grid for the multi-grid launch
 // (written once per grid set-up; read by the kernel with generic loads, its
@@ -148,7 +155,7 @@ int64_t fused_units(int K, int nx, int ny);
 cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, int64_t total_units,
                                int flip, int *err, cudaStream_t st);
 
-// Build a 3-D FP32 tensor map over `planes` (2 or 3) consecutive pitched
+// Build a 3-D FP32 tensor map over `planes` (2 to 4) consecutive pitched
 // planes (nx x ny each, `plane_bytes` apart) for the fused path: one box
 // load fetches the same rows of every plane.  Returns false (and a message)
 // if the driver entry point is unavailable or the encode call fails.

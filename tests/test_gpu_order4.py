@@ -1,10 +1,12 @@
 """Fourth-order Suzuki steps (Sec. 2, Eq. fourthorder) on the GPU vs the FP64
 oracle's order-4 evolution, through the C ABI.
 
-U4(dt) = U2(p dt)^2 U2((1-4p) dt) U2(p dt)^2 with p = 1/(4 - 4^(1/3)); the
-GPU runs the p dt substeps of neighbouring steps as fused launches and each
-(1-4p) dt substep as a depth-1 launch with its own phase table.  Tolerances
-as for the second-order path: FP64 1e-12, FP32 1e-5 relative L2.
+U4(dt) = U2(p dt)^2 U2((1-4p) dt) U2(p dt)^2 with p = 1/(4 - 4^(1/3)).  With
+K = 0 the GPU applies each U4 step in one launch of the fused kernel (five
+substeps, two phase tables in one box); with K >= 1 it runs the p dt substeps
+of neighbouring steps as fused launches of depth <= K and each (1-4p) dt
+substep as a depth-1 launch.  Tolerances as for the second-order path: FP64
+1e-12, FP32 1e-5 relative L2.
 """
 import os
 
@@ -123,10 +125,12 @@ def test_fourth_order_convergence_on_the_gpu():
     assert errs[2] < 0.05 * np.linalg.norm(cplx(e2re, e2im) - exact)
 
 
-@pytest.mark.parametrize("K,steps,expected", [(0, 5, 11), (4, 1, 3), (3, 5, 15), (2, 3, 9)])
+@pytest.mark.parametrize("K,steps,expected", [(0, 5, 5), (4, 5, 11), (4, 1, 3), (3, 5, 15),
+                                               (2, 3, 9)])
 def test_launch_sequence(K, steps, expected):
-    """Per run of a substeps ceil(r / depth) launches, plus one per b substep:
-    depth 4 gives 1 + 2 n launches for n steps, depth 3 gives 3 n."""
+    """K = 0: one launch per step (all five substeps fused).  K >= 1: per run
+    of a substeps ceil(r / K) launches, plus one per b substep: depth 4 gives
+    1 + 2 n launches for n steps, depth 3 gives 3 n."""
     rng = np.random.default_rng(8)
     re, im = random_state(rng, 64, 64)
     g = trotter.Grid(64, 64, "f32")
