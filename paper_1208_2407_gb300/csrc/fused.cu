@@ -105,14 +105,17 @@ constexpr uint32_t FULL = 0xffffffffu;
 // lengths (gamma_a, s_a, gamma_b, s_b).
 __host__ __device__ constexpr int phase_planes(int mode) { return mode == 3 ? 3 : mode == 4 ? 4 : 2; }
 
+// __launch_bounds__ minimum resident blocks of the single-grid kernel
+__host__ __device__ constexpr int min_blocks(int K)
+{
+    return K == 3 ? TS_FUSED_MIN_BLOCKS_K3 : K == 4 ? TS_FUSED_MIN_BLOCKS_K4 : TS_FUSED_MIN_BLOCKS;
+}
+
 template <int K, int PP = 2>
 struct Cfg {
     static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
     static constexpr int PF = K == 1 ? TS_FUSED_PF_K1 : K == 2 ? TS_FUSED_PF_K2 : TS_FUSED_PF_DEEP;
     static constexpr bool PINGPONG = K >= TS_FUSED_PINGPONG_MIN_K && K <= TS_FUSED_PINGPONG_MAX_K;
-    static constexpr int MINB = K == 3   ? TS_FUSED_MIN_BLOCKS_K3
-                                : K == 4 ? TS_FUSED_MIN_BLOCKS_K4
-                                         : TS_FUSED_MIN_BLOCKS;
     // packed FP32 FMAs in the Y sweeps and the phase: 0 never, 1 for every
     // depth but 2 (where the scalar form measured faster), 2 always
     static constexpr bool PACKED = TS_FUSED_FFMA2 == 2 || (TS_FUSED_FFMA2 == 1 && K != 2);
@@ -819,7 +822,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
 // One grid; the (strip, row-pair) units are split into equal contiguous
 // ranges, one per warp of a persistent launch.
 template <int K, int MODE>
-__global__ void __launch_bounds__(Cfg<K>::WPC * 32, Cfg<K>::MINB)
+__global__ void __launch_bounds__(Cfg<K>::WPC * 32, min_blocks(K))
 fused_kernel(const __grid_constant__ CUtensorMap tm_state,
              const __grid_constant__ CUtensorMap tm_phase, const KParams p)
 {
