@@ -913,24 +913,35 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
     }
 }
 
+// Resident blocks per SM and SM count of a kernel at its dynamic shared
+// memory size, set up once per kernel (the first caller's function-local
+// static initialisation, which C++ runs exactly once even when threads race).
+struct Occupancy {
+    cudaError_t err;
+    int blocks_per_sm, num_sms;
+};
+
+template <typename F>
+Occupancy occupancy_of(F kernel, int threads, int smem)
+{
+    Occupancy o = {cudaSuccess, 0, 0};
+    o.err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (o.err != cudaSuccess) return o;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&o.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    o.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.blocks_per_sm, kernel, threads, smem);
+    if (o.err == cudaSuccess && o.blocks_per_sm < 1) o.err = cudaErrorInvalidConfiguration;
+    return o;
+}
+
 template <int K, int MODE>
 cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
 {
     using C = Cfg<K, phase_planes(MODE)>;
-    static int blocks_per_sm = -1;
-    static int num_sms = 0;
-    if (blocks_per_sm < 0) {
-        cudaError_t e = cudaFuncSetAttribute(fused_kernel<K, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fused_kernel<K, MODE>,
-                                                          C::WPC * 32, C::SMEM);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
-    }
+    static const Occupancy occ = occupancy_of(fused_kernel<K, MODE>, C::WPC * 32, C::SMEM);
+    if (occ.err != cudaSuccess) return occ.err;
+    const int blocks_per_sm = occ.blocks_per_sm, num_sms = occ.num_sms;
     KParams p;
     p.out_re = a.out_re;
     p.out_im = a.out_im;
@@ -1003,31 +1014,17 @@ int64_t fused_units(int K, int nx, int ny)
 }
 
 template <int K>
-struct MultiOcc {
-    static int blocks_per_sm, num_sms;
-};
-template <int K> int MultiOcc<K>::blocks_per_sm = -1;
-template <int K> int MultiOcc<K>::num_sms = 0;
+const Occupancy &multi_occupancy()
+{
+    using C = Cfg<K>;
+    static const Occupancy occ = occupancy_of(fused_multi_kernel<K>, C::WPC * 32, C::SMEM);
+    return occ;
+}
 
 template <int K>
 cudaError_t prepare_multi_k()
 {
-    using C = Cfg<K>;
-    int &blocks_per_sm = MultiOcc<K>::blocks_per_sm;
-    int &num_sms = MultiOcc<K>::num_sms;
-    if (blocks_per_sm < 0) {
-        cudaError_t e = cudaFuncSetAttribute(fused_multi_kernel<K>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fused_multi_kernel<K>,
-                                                          C::WPC * 32, C::SMEM);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
-    }
-    return cudaSuccess;
+    return multi_occupancy<K>().err;
 }
 
 template <int K>
@@ -1035,9 +1032,9 @@ cudaError_t launch_multi_k(const EpochEntry *tab, int n_grids, int64_t total_uni
                            int *err, cudaStream_t st)
 {
     using C = Cfg<K>;
-    cudaError_t pe = prepare_multi_k<K>();
-    if (pe != cudaSuccess) return pe;
-    const int blocks_per_sm = MultiOcc<K>::blocks_per_sm, num_sms = MultiOcc<K>::num_sms;
+    const Occupancy &occ = multi_occupancy<K>();
+    if (occ.err != cudaSuccess) return occ.err;
+    const int blocks_per_sm = occ.blocks_per_sm, num_sms = occ.num_sms;
     int64_t want = (total_units + 15) / 16;
     int64_t cap = (int64_t)num_sms * blocks_per_sm * C::WPC;
     const int total_warps = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
@@ -1103,17 +1100,19 @@ cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st)
 bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
                           size_t plane_bytes, const char **why, int planes)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
+    // looked up once (thread-safe static initialisation)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() {
         cudaDriverEntryPointQueryResult qr;
         void *fn = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                              cudaEnableDefault, &qr) != cudaSuccess ||
-            qr != cudaDriverEntryPointSuccess || !fn) {
-            *why = "cuTensorMapEncodeTiled is not available from the driver";
-            return false;
-        }
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+            qr != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) {
+        *why = "cuTensorMapEncodeTiled is not available from the driver";
+        return false;
     }
     if (planes < 1 || planes > 4) {
         *why = "tensor map: 1 to 4 planes";
