@@ -140,10 +140,10 @@ ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
  *     p = 1 / (4 - 4^(1/3)),
  * where each substep U2(w dt) uses the kinetic angle w theta and the phase
  * exp(-i V w dt) (w = 1 - 4p is negative: that substep runs backwards).  The
- * grid's phase planes then hold the table at p dt; four more planes of
- * ts_layout.plane_bytes (the tables at p dt and (1-4p) dt side by side) are
- * cudaMalloc'd by the library on the first order-4 call and freed by
- * ts_destroy_grid, also for grids on a caller-provided slab.  Fourth-order grids are evolved one by one
+ * grid's phase planes then hold the table at p dt, and a second table at
+ * (1-4p) dt (two planes of ts_layout.plane_bytes) is cudaMalloc'd by the
+ * library on the first order-4 call and freed by ts_destroy_grid, also for
+ * grids on a caller-provided slab.  Fourth-order grids are evolved one by one
  * by ts_evolve_batched and are refused by the adjoint calls
  * (TS_ERR_UNSUPPORTED).  Errors: TS_ERR_ARG (order not 2 or 4, non-finite dt
  * or theta), TS_ERR_OOM (the second table), TS_ERR_CUDA. */

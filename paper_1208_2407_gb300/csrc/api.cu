@@ -481,22 +481,18 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
     cudaError_t e;
     // fourth order (Eq. fourthorder): U4(dt) = U2(p dt)^2 U2((1-4p) dt) U2(p dt)^2
     // with p = 1 / (4 - 4^(1/3)); substep a = p dt uses planes 4/5, substep
-    // b = (1 - 4p) dt a second table.  Both tables also sit side by side in
-    // four library-owned planes (a, then b), so that one box load gives the
-    // fused fourth-order kernel both.
+    // b = (1 - 4p) dt a second table in two library-owned planes
     const double p4 = 1.0 / (4.0 - std::cbrt(4.0));
     const double w[2] = {p4, 1.0 - 4.0 * p4};
     const size_t PB = g->L.plane_bytes;
     if (order == 4 && !g->tab_b) {
         unsigned char *tb = nullptr;
-        e = cudaMalloc((void **)&tb, 4 * PB);
+        e = cudaMalloc((void **)&tb, 2 * PB);
         if (e != cudaSuccess) return fail(TS_ERR_OOM, "ts_set_potential_order: second table: %s",
                                           cudaGetErrorString(e));
         if (!g->f64()) {
             const char *why = "";
-            if (!ts::make_pair_tensor_map(&g->tm_phase_b, tb + 2 * PB, nx, ny, g->L.pitch, PB,
-                                          &why) ||
-                !ts::make_pair_tensor_map(&g->tm_u4, tb, nx, ny, g->L.pitch, PB, &why, 4)) {
+            if (!ts::make_pair_tensor_map(&g->tm_phase_b, tb, nx, ny, g->L.pitch, PB, &why)) {
                 cudaFree(tb);
                 return fail(TS_ERR_CUDA, "ts_set_potential_order: %s", why);
             }
@@ -509,7 +505,7 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
         for (int i = 0; i < 2; ++i) g->sub[i] = ts::rot_coef(w[i] * theta);
     if (!V) {
         e = cudaMemsetAsync(g->pg(), 0, 3 * g->L.plane_bytes, st);   // planes 4, 5, 6
-        if (e == cudaSuccess && order == 4) e = cudaMemsetAsync(g->tab_b, 0, 4 * PB, st);
+        if (e == cudaSuccess && order == 4) e = cudaMemsetAsync(g->tab_b, 0, 2 * PB, st);
         if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: clear");
         return TS_OK;
     }
@@ -525,8 +521,6 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
     if (e == cudaSuccess && order == 4)
         e = ts::launch_phase_table(src, g->pg_b(), g->ps_b(), g->vp(), g->f64(), nx, ny,
                                    g->L.pitch, w[1] * dt, st);
-    if (e == cudaSuccess && order == 4)   // the a table next to the b table
-        e = cudaMemcpyAsync(g->tab_b, g->pg(), 2 * PB, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: table kernel");
     if (where == TS_HOST) {
         e = cudaStreamSynchronize(st);
@@ -754,7 +748,8 @@ ts_status evolve_driven(ts_grid *g, int64_t steps, int K, bool plain, cudaStream
 
 // Fourth-order steps, each one launch of the fused kernel over all five
 // substeps a a b a a (the merged boundaries inside the step use the angles
-// 2a, a + b, a + b, 2a): 32 B per site and U4 step.
+// 2a, a + b, a + b, 2a; the a table streams through the phase ring, the b
+// table through a shorter ring of its own): 32 B per site and U4 step.
 ts_status fused_u4_steps(ts_grid *g, int64_t steps, cudaStream_t st)
 {
     if (!g->tmaps_ok) return fail(TS_ERR_STATE, "fused path: tensor maps missing");
@@ -764,7 +759,8 @@ ts_status fused_u4_steps(ts_grid *g, int64_t steps, cudaStream_t st)
     for (int64_t n = 0; n < steps; ++n) {
         ts::FusedLaunch a;
         a.tm_state = &g->tm_state[g->cur];
-        a.tm_phase = &g->tm_u4;
+        a.tm_phase = &g->tm_phase;
+        a.tm_b = &g->tm_phase_b;
         a.out_re = (float *)g->re_other();
         a.out_im = (float *)g->im_other();
         a.nx = (int)g->L.nx;

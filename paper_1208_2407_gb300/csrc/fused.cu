@@ -101,9 +101,10 @@ constexpr uint32_t FULL = 0xffffffffu;
 // Shallow pipelines (K <= 2) are memory bound and prefetch deeper; deep ones
 // are arithmetic bound and keep shared memory small for occupancy.
 // Planes of a phase-ring slot: (gamma_V, s_V); with a drive (MODE 3) also
-// V1; for the fused fourth-order step (MODE 4) the tables of both substep
-// lengths (gamma_a, s_a, gamma_b, s_b).
-__host__ __device__ constexpr int phase_planes(int mode) { return mode == 3 ? 3 : mode == 4 ? 4 : 2; }
+// V1.  The fused fourth-order step (MODE 4) keeps the a substep's table in
+// the phase ring and the b substep's in a third, shorter ring (the b ring):
+// only substep 2 reads it, at iterations j + 2 and j + 3 of row pair j.
+__host__ __device__ constexpr int phase_planes(int mode) { return mode == 3 ? 3 : 2; }
 
 // __launch_bounds__ minimum resident blocks of the single-grid kernel
 __host__ __device__ constexpr int min_blocks(int K)
@@ -111,7 +112,7 @@ __host__ __device__ constexpr int min_blocks(int K)
     return K == 3 ? TS_FUSED_MIN_BLOCKS_K3 : K == 4 ? TS_FUSED_MIN_BLOCKS_K4 : TS_FUSED_MIN_BLOCKS;
 }
 
-template <int K, int PP = 2>
+template <int K, int PP = 2, bool BRING = false>
 struct Cfg {
     static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
     static constexpr int PF = K == 1 ? TS_FUSED_PF_K1 : K == 2 ? TS_FUSED_PF_K2 : TS_FUSED_PF_DEEP;
@@ -125,8 +126,12 @@ struct Cfg {
     static constexpr int VALID = FUSED_BOX_COLS - 2 * HALO;
     // a phase slot holds (gamma_V, s_V) and, with a drive, the V1 rows too
     static constexpr int PSLOT = PP * PLANE_SLOT_BYTES;
-    static constexpr int WARP_SMEM = NSS * SLOT_BYTES + NSP * PSLOT;
-    static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + (NSS + NSP) * 8);
+    // b ring (MODE 4): row pair r is read at iterations r + 2 and r + 3 and
+    // waited for at r + 2, so the ring holds r in [j - 3, j - 2 + PF]
+    static constexpr int NSB = BRING ? PF + 2 : 0;
+    static constexpr int NBAR = NSS + NSP + NSB;   // mbarriers per warp
+    static constexpr int WARP_SMEM = NSS * SLOT_BYTES + NSP * PSLOT + NSB * SLOT_BYTES;
+    static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + NBAR * 8);
 };
 
 struct Frag {
@@ -483,13 +488,14 @@ template <int K, bool INTERIOR, int MODE>
 __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&cout)[2 * K],
                                               Frag a, Frag b, int yin, int j,
                                               const unsigned char *ring_p, int pos_p,
+                                              const unsigned char *ring_b, int cnt_b,
                                               const StripCoef &c, const KParams &p, int lane,
                                               const Owned &w, Frag &O0, Frag &O1)
 {
     static_assert(MODE == 0 || MODE == 3 || MODE == 4 || K == 1,
                   "mid-step modes exist for K = 1 only");
     static_assert(MODE != 4 || K == 5, "the fused fourth-order step has five substeps");
-    using C = Cfg<K, phase_planes(MODE)>;
+    using C = Cfg<K, phase_planes(MODE), MODE == 4>;
     // MODE 4: substep k of U4 = a a b a a is b for k == 2 (angle and table)
     auto is_b = [](int k) { return MODE == 4 && k == 2; };
     constexpr int NSP = C::NSP;
@@ -501,6 +507,9 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
         int q = pos_p - back;
         if (q < 0) q += NSP;
         return ring_p + q * C::PSLOT;
+    };
+    auto slot_b = [&](int back) -> const unsigned char * {   // b-ring slot of row pair j - back
+        return ring_b + ((cnt_b + j - back) % (C::NSB > 0 ? C::NSB : 1)) * SLOT_BYTES;
     };
     // step 0, first half: Xe, Xo (row-local), Ye aligned, Yo shifted
     x_even(a, c.E1);
@@ -576,16 +585,16 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
         Q = P2;
         y1 -= 2;
         // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
-        // (MODE 4: the b substep reads the slot's second table, planes 2, 3)
-        const int tpl = bk ? 2 : 0;
+        // (MODE 4: the b substep's table comes from the b ring)
+        auto slot_k = [&](int back) { return bk ? slot_b(back) : slot_p(back); };
         if (INTERIOR || j - k - 1 >= 0) {
-            const unsigned char *sp = slot_p(k + 1);
-            phase4<C::PACKED>(P, lds4(sp, tpl, 1, lane), lds4(sp, tpl + 1, 1, lane));
+            const unsigned char *sp = slot_k(k + 1);
+            phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
             if constexpr (MODE == 3) drive4<C::PACKED>(P, lds4(sp, 2, 1, lane), p.adt[k]);
         }
         if (INTERIOR || j - k >= 0) {
-            const unsigned char *sp = slot_p(k);
-            phase4<C::PACKED>(Q, lds4(sp, tpl, 0, lane), lds4(sp, tpl + 1, 0, lane));
+            const unsigned char *sp = slot_k(k);
+            phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), lds4(sp, 1, 0, lane));
             if constexpr (MODE == 3) drive4<C::PACKED>(Q, lds4(sp, 2, 0, lane), p.adt[k]);
         }
     }
@@ -611,30 +620,37 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
 // mbarrier phase parities of the next row pair to be consumed (they carry
 // over from one row range to the next).
 struct WarpRings {
-    uint64_t *bar_s, *bar_p;
-    unsigned char *ring_s, *ring_p;
+    uint64_t *bar_s, *bar_p, *bar_b;
+    unsigned char *ring_s, *ring_p, *ring_b;
     int pos_s, pos_p;
     uint32_t par_s, par_p;
+    // b ring: b copies are numbered across the warp's segments; copy L sits
+    // in slot L % NSB with mbarrier phase parity (L / NSB) & 1, and cnt_b
+    // copies came before the current segment (row pair r is copy cnt_b + r)
+    int cnt_b;
 };
 
-template <int K, int PP = 2>
+template <int K, int PP = 2, bool BRING = false>
 __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int warp, int lane)
 {
-    using C = Cfg<K, PP>;
-    constexpr int NSS = C::NSS, NSP = C::NSP;
+    using C = Cfg<K, PP, BRING>;
+    constexpr int NSS = C::NSS, NSP = C::NSP, NBAR = C::NBAR;
     WarpRings r;
-    // barriers first, then 1 KiB-aligned slots (state ring, phase ring)
-    r.bar_s = reinterpret_cast<uint64_t *>(smem_raw) + warp * (NSS + NSP);
+    // barriers first, then 1 KiB-aligned slots (state ring, phase ring, b ring)
+    r.bar_s = reinterpret_cast<uint64_t *>(smem_raw) + warp * NBAR;
     r.bar_p = r.bar_s + NSS;
+    r.bar_b = r.bar_p + NSP;
     const uint32_t base_addr = smem_addr(smem_raw);
     const uint32_t slots_off =
-        ((base_addr + C::WPC * (NSS + NSP) * 8 + 1023u) & ~1023u) - base_addr;
+        ((base_addr + C::WPC * NBAR * 8 + 1023u) & ~1023u) - base_addr;
     r.ring_s = smem_raw + slots_off + (size_t)warp * C::WARP_SMEM;
     r.ring_p = r.ring_s + NSS * SLOT_BYTES;
+    r.ring_b = r.ring_p + NSP * C::PSLOT;
     r.pos_s = r.pos_p = 0;
     r.par_s = r.par_p = 0;
+    r.cnt_b = 0;
     if (lane == 0) {
-        for (int i = 0; i < NSS + NSP; ++i) mbar_init(&r.bar_s[i], 1);
+        for (int i = 0; i < NBAR; ++i) mbar_init(&r.bar_s[i], 1);
         fence_mbar_init();
     }
     __syncwarp();
@@ -647,7 +663,7 @@ __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int wa
 // outstanding copies are drained).
 // Per-segment constants of one warp.
 struct Seg {
-    const CUtensorMap *tm_state, *tm_phase;
+    const CUtensorMap *tm_state, *tm_phase, *tm_b;
     int XL, xg, Y0, Y1, Ys, n_iter, lane;
     bool store_lane;
     StripCoef c;
@@ -661,6 +677,23 @@ __device__ __forceinline__ void issue_state(WarpRings &r, const Seg &s, int pos,
     tma_load_pair(r.ring_s + pos * SLOT_BYTES, s.tm_state, s.XL, s.Ys + 2 * j, &r.bar_s[pos]);
 }
 
+// b ring (MODE 4): the b substep's (gamma, s) rows of row pair j, copy
+// number r.cnt_b + j
+template <int NSB>
+__device__ __forceinline__ void issue_b(WarpRings &r, const Seg &s, int j)
+{
+    const int pos = (r.cnt_b + j) % NSB;
+    mbar_expect_tx(&r.bar_b[pos], SLOT_BYTES);
+    tma_load_pair(r.ring_b + pos * SLOT_BYTES, s.tm_b, s.XL, s.Ys + 2 * j, &r.bar_b[pos]);
+}
+
+template <int NSB>
+__device__ __forceinline__ bool wait_b(const WarpRings &r, int j, uint64_t limit)
+{
+    const int L = r.cnt_b + j;
+    return mbar_wait(&r.bar_b[L % NSB], (uint32_t)(L / NSB) & 1u, limit);
+}
+
 template <int K, int PP = 2>
 __device__ __forceinline__ void issue_phase(WarpRings &r, const Seg &s, int pos, int j)
 {
@@ -672,27 +705,37 @@ __device__ __forceinline__ void issue_phase(WarpRings &r, const Seg &s, int pos,
 // Row pair j of a segment: wait for its slots, run the pipeline, store the
 // finished rows, refill the freed slots.  Returns false if a bounded wait
 // gave up (after setting the error bit and draining this warp's copies).
+// Copies issued so far into each ring of a segment (row pairs [0, n)).
+struct Issued {
+    int s, p, b;
+};
+
 template <int K, int MODE, bool INTERIOR>
 __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KParams &p, int j,
                                          const Frag (&cin)[2 * K], Frag (&cout)[2 * K],
-                                         int &issued_s, int &issued_p)
+                                         Issued &iss)
 {
-    using C = Cfg<K, phase_planes(MODE)>;
-    constexpr int NSS = C::NSS, NSP = C::NSP;
+    using C = Cfg<K, phase_planes(MODE), MODE == 4>;
+    constexpr int NSS = C::NSS, NSP = C::NSP, NSB = C::NSB;
     const int lane = s.lane;
     bool ok = mbar_wait(&r.bar_s[r.pos_s], r.par_s, WAIT_LIMIT_NS) &&
               mbar_wait(&r.bar_p[r.pos_p], r.par_p, WAIT_LIMIT_NS);
+    if constexpr (MODE == 4)   // row pair j - 2's b rows, first read now
+        ok = ok && (j < 2 || wait_b<NSB>(r, j - 2, WAIT_LIMIT_NS));
     ok = __all_sync(FULL, ok);
     if (!ok) {
         if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
         // drain this warp's outstanding copies (bounded) before leaving
-        for (int jj = j, ps = r.pos_s, ph = r.par_s; jj < issued_s; ++jj) {
+        for (int jj = j, ps = r.pos_s, ph = r.par_s; jj < iss.s; ++jj) {
             mbar_wait(&r.bar_s[ps], ph, WAIT_LIMIT_NS / 4);
             if (++ps == NSS) { ps = 0; ph ^= 1u; }
         }
-        for (int jj = j, ps = r.pos_p, ph = r.par_p; jj < issued_p; ++jj) {
+        for (int jj = j, ps = r.pos_p, ph = r.par_p; jj < iss.p; ++jj) {
             mbar_wait(&r.bar_p[ps], ph, WAIT_LIMIT_NS / 4);
             if (++ps == NSP) { ps = 0; ph ^= 1u; }
+        }
+        if constexpr (MODE == 4) {
+            for (int jj = j < 2 ? 0 : j - 2; jj < iss.b; ++jj) wait_b<NSB>(r, jj, WAIT_LIMIT_NS / 4);
         }
         return false;
     }
@@ -704,8 +747,8 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     b.im = lds4(sj, 1, 1, lane);
     const int yin = s.Ys + 2 * j;
     Frag O0, O1;
-    pipeline_step<K, INTERIOR, MODE>(cin, cout, a, b, yin, j, r.ring_p, r.pos_p, s.c, p, lane,
-                                     s.own, O0, O1);
+    pipeline_step<K, INTERIOR, MODE>(cin, cout, a, b, yin, j, r.ring_p, r.pos_p, r.ring_b,
+                                     r.cnt_b, s.c, p, lane, s.own, O0, O1);
     const int yo = yin - 2 * K;
     if (s.store_lane && yo >= s.Y0 && yo < s.Y1) {
         float *rr = p.out_re + (int64_t)yo * p.pitch + s.xg;
@@ -720,18 +763,24 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
         }
     }
     // state slot j and phase slot j-K are no longer read: refill them with
-    // row pairs j + NSS and j - K + NSP (the same ring positions)
+    // row pairs j + NSS and j - K + NSP (the same ring positions); MODE 4
+    // also refills b slot j-3 with row pair j - 3 + NSB
     __syncwarp();
-    const int js = j + NSS, jp = j - K + NSP;
+    const int js = j + NSS, jp = j - K + NSP, jb = j - 3 + NSB;
     const bool more_s = js < s.n_iter, more_p = j >= K && jp < s.n_iter;
-    if (lane == 0 && (more_s || more_p)) {
+    const bool more_b = MODE == 4 && j >= 3 && jb < s.n_iter;
+    if (lane == 0 && (more_s || more_p || more_b)) {
         fence_proxy_async();
         if (more_s) issue_state<K>(r, s, r.pos_s, js);
         if (more_p)
             issue_phase<K, phase_planes(MODE)>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
+        if constexpr (MODE == 4) {
+            if (more_b) issue_b<NSB>(r, s, jb);   // the slot row pair j - 3 leaves
+        }
     }
-    issued_s += more_s;
-    issued_p += more_p;
+    iss.s += more_s;
+    iss.p += more_p;
+    iss.b += more_b;
     if (++r.pos_s == NSS) { r.pos_s = 0; r.par_s ^= 1u; }
     if (++r.pos_p == NSP) { r.pos_p = 0; r.par_p ^= 1u; }
     return true;
@@ -742,14 +791,16 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
 // false if a bounded wait gave up.
 template <int K, int MODE>
 __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_state,
-                                            const CUtensorMap *tm_phase, const KParams &p,
-                                            int sx, int q0, int q1, int lane)
+                                            const CUtensorMap *tm_phase, const CUtensorMap *tm_b,
+                                            const KParams &p, int sx, int q0, int q1, int lane)
 {
-    using C = Cfg<K, phase_planes(MODE)>;
-    constexpr int NSS = C::NSS, NSP = C::NSP, HALO = C::HALO, VALID = C::VALID;
+    using C = Cfg<K, phase_planes(MODE), MODE == 4>;
+    constexpr int NSS = C::NSS, NSP = C::NSP, NSB = C::NSB, HALO = C::HALO, VALID = C::VALID;
+    static_assert(NSB <= NSP, "the prologue issues the b ring inside the phase ring's loop");
     Seg s;
     s.tm_state = tm_state;
     s.tm_phase = tm_phase;
+    s.tm_b = tm_b;
     s.lane = lane;
     s.XL = sx * VALID - HALO;            // first loaded column (multiple of 4)
     s.xg = s.XL + 4 * lane;              // this lane's first column
@@ -777,14 +828,18 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
 
     const int n_pro_s = s.n_iter < NSS ? s.n_iter : NSS;
     const int n_pro_p = s.n_iter < NSP ? s.n_iter : NSP;
+    const int n_pro_b = s.n_iter < NSB ? s.n_iter : NSB;
     if (lane == 0) {
         fence_proxy_async();
         for (int j = 0; j < n_pro_p; ++j) {
             if (j < n_pro_s) issue_state<K>(r, s, (r.pos_s + j) % NSS, j);
             issue_phase<K, phase_planes(MODE)>(r, s, (r.pos_p + j) % NSP, j);
+            if constexpr (MODE == 4) {
+                if (j < n_pro_b) issue_b<NSB>(r, s, j);
+            }
         }
     }
-    int issued_s = n_pro_s, issued_p = n_pro_p;
+    Issued iss = {n_pro_s, n_pro_p, n_pro_b};
 
     // Carried rows: interior row pairs go in twos; for deep pipelines the
     // first reads set A and writes set B and the second goes back into A, so
@@ -801,19 +856,31 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     for (int j = 0; j < s.n_iter;) {
         if (j + 1 < s.n_iter && interior(j) && interior(j + 1)) {
             if (C::PINGPONG) {
-                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cB, issued_s, issued_p)) return false;
-                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cB, cA, issued_s, issued_p))
+                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cB, iss)) return false;
+                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cB, cA, iss))
                     return false;
             } else {
-                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cA, issued_s, issued_p)) return false;
-                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cA, cA, issued_s, issued_p))
+                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cA, iss)) return false;
+                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cA, cA, iss))
                     return false;
             }
             j += 2;
         } else {
-            if (!row_pair<K, MODE, false>(r, s, p, j, cA, cA, issued_s, issued_p)) return false;
+            if (!row_pair<K, MODE, false>(r, s, p, j, cA, cA, iss)) return false;
             j += 1;
         }
+    }
+    if constexpr (MODE == 4) {
+        // the last two row pairs' b rows were never needed: let their copies
+        // land before the slots are reused, then number the next segment's on
+        bool ok = true;
+        for (int jj = s.n_iter - 2 < 0 ? 0 : s.n_iter - 2; jj < s.n_iter; ++jj)
+            ok = wait_b<NSB>(r, jj, WAIT_LIMIT_NS) && ok;
+        if (!__all_sync(FULL, ok)) {
+            if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
+            return false;
+        }
+        r.cnt_b += s.n_iter;
     }
     __syncwarp();
     return true;
@@ -824,13 +891,14 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
 template <int K, int MODE>
 __global__ void __launch_bounds__(Cfg<K>::WPC * 32, min_blocks(K))
 fused_kernel(const __grid_constant__ CUtensorMap tm_state,
-             const __grid_constant__ CUtensorMap tm_phase, const KParams p)
+             const __grid_constant__ CUtensorMap tm_phase,
+             const __grid_constant__ CUtensorMap tm_b, const KParams p)
 {
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * Cfg<K>::WPC + warp;
     if (gw >= p.total_warps) return;
-    WarpRings r = carve_rings<K, phase_planes(MODE)>(smem_raw, warp, lane);
+    WarpRings r = carve_rings<K, phase_planes(MODE), MODE == 4>(smem_raw, warp, lane);
     if (p.strip_warps > 0) {
         // strip-aligned split: warp (sx, i) takes row range i of strip sx, so
         // warps of neighbouring strips walk the same rows at the same time and
@@ -838,7 +906,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
         const int sx = gw / p.strip_warps, i = gw - sx * p.strip_warps;
         const int q0 = (int)((int64_t)i * p.n_pairs / p.strip_warps);
         const int q1 = (int)((int64_t)(i + 1) * p.n_pairs / p.strip_warps);
-        if (q1 > q0) run_segment<K, MODE>(r, &tm_state, &tm_phase, p, sx, q0, q1, lane);
+        if (q1 > q0) run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, p, sx, q0, q1, lane);
         return;
     }
     const int64_t u_begin = (int64_t)gw * p.units / p.total_warps;
@@ -849,7 +917,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
         const int64_t q1_want = (int64_t)q0 + (u_end - u);
         const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
         u += q1 - q0;
-        if (!run_segment<K, MODE>(r, &tm_state, &tm_phase, p, sx, q0, q1, lane)) return;
+        if (!run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, p, sx, q0, q1, lane)) return;
     }
 }
 
@@ -909,7 +977,7 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
         if (q1_want > q0 + left_in_grid) q1_want = q0 + left_in_grid;
         const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
         u += q1 - q0;
-        if (!run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, p, sx, q0, q1, lane)) return;
+        if (!run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, p, sx, q0, q1, lane)) return;
     }
 }
 
@@ -938,7 +1006,7 @@ Occupancy occupancy_of(F kernel, int threads, int smem)
 template <int K, int MODE>
 cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
 {
-    using C = Cfg<K, phase_planes(MODE)>;
+    using C = Cfg<K, phase_planes(MODE), MODE == 4>;
     static const Occupancy occ = occupancy_of(fused_kernel<K, MODE>, C::WPC * 32, C::SMEM);
     if (occ.err != cudaSuccess) return occ.err;
     const int blocks_per_sm = occ.blocks_per_sm, num_sms = occ.num_sms;
@@ -984,7 +1052,8 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.tab = a.tab;
     p.sab = a.sab;
     const int blocks = (p.total_warps + C::WPC - 1) / C::WPC;
-    fused_kernel<K, MODE><<<blocks, C::WPC * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
+    fused_kernel<K, MODE><<<blocks, C::WPC * 32, C::SMEM, st>>>(
+        *a.tm_state, *a.tm_phase, a.tm_b ? *a.tm_b : *a.tm_phase, p);
     count_launches(1);
     return cudaGetLastError();
 }

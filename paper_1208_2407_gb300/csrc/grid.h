@@ -32,10 +32,9 @@ struct ts_grid {
     double g1, s1, t1, s2, t2;   // rotation coefficients (FP64): theta and 2 theta
     int order;                   // 2: U2(dt) per step; 4: U4(dt) (ts_set_potential_order)
     ts::RotCoef sub[2];          // order 4: substeps p dt and (1 - 4p) dt
-    unsigned char *tab_b;        // order 4, library-owned: (gamma_V, s_V) at p dt, then at
-                                 // (1 - 4p) dt; planes 4/5 also hold the table at p dt
-    CUtensorMap tm_phase_b;      // the (1 - 4p) dt table
-    CUtensorMap tm_u4;           // all four planes (the fused fourth-order step)
+    unsigned char *tab_b;        // order 4: (gamma_V, s_V) at (1 - 4p) dt, library-owned;
+                                 // planes 4/5 then hold the table at p dt
+    CUtensorMap tm_phase_b;
     // time-dependent potential V0 + a_n V1 (ts_set_drive): a library-owned
     // slab of three planes (copies of gamma_V, s_V, then V1), its tensor map,
     // the amplitudes a_n and the index of the next one
@@ -60,8 +59,8 @@ struct ts_grid {
     void *ps() const { return plane(5); }
     void *vp() const { return plane(6); }
     void *drive_v1() const { return drive_slab + 2 * L.plane_bytes; }
-    void *pg_b() const { return tab_b + 2 * L.plane_bytes; }
-    void *ps_b() const { return tab_b + 3 * L.plane_bytes; }
+    void *pg_b() const { return tab_b; }
+    void *ps_b() const { return tab_b + L.plane_bytes; }
     bool f64() const { return L.dtype == TS_F64; }
     // rows of every plane: ny per slab, nz slabs (3-D grids; nz = 1 in 2-D)
     int64_t rows() const { return L.ny * L.nz; }

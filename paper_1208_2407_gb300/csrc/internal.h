@@ -88,6 +88,7 @@ cudaError_t launch_inner(const float *phi_re, const float *phi_im, const float *
 struct FusedLaunch {
     const CUtensorMap *tm_state;   // (re, im) planes of the input pair, 3-D map
     const CUtensorMap *tm_phase;   // (gamma_V, s_V) planes, 3-D map
+    const CUtensorMap *tm_b = nullptr;   // launch_fused_u4: the b substep's table
     float *out_re, *out_im;
     int nx, ny;
     int64_t pitch;
@@ -122,7 +123,7 @@ cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st);
 constexpr int FUSED_DRIVE_MAX_K = 4;
 cudaError_t launch_fused_drive(int K, const FusedLaunch &a, cudaStream_t st);
 // One fourth-order step U4 = a a b a a in one launch (five substeps, depth
-// 5): tm_phase maps four planes (gamma_a, s_a, gamma_b, s_b).
+// 5): tm_phase maps the a substep's table, tm_b the b substep's.
 cudaError_t launch_fused_u4(const FusedLaunch &a, cudaStream_t st);
 
 // Device-resident description of one FP32 grid for the multi-grid launch
