@@ -76,6 +76,12 @@ namespace {
 #ifndef TS_FUSED_MIN_BLOCKS_K4   // ... for K = 4
 #define TS_FUSED_MIN_BLOCKS_K4 1
 #endif
+#ifndef TS_FUSED_MULTI_MIN_BLOCKS_K3   // multi-grid kernel, K = 3
+#define TS_FUSED_MULTI_MIN_BLOCKS_K3 1
+#endif
+#ifndef TS_FUSED_MULTI_MIN_BLOCKS_K4   // multi-grid kernel, K = 4
+#define TS_FUSED_MULTI_MIN_BLOCKS_K4 1
+#endif
 #ifndef TS_FUSED_PINGPONG_MIN_K  // interior row pairs alternate two carry sets for K in
 #define TS_FUSED_PINGPONG_MIN_K 3    // [MIN_K, MAX_K] (beyond MAX_K the second set spills)
 #endif
@@ -110,6 +116,14 @@ __host__ __device__ constexpr int phase_planes(int mode) { return mode == 3 ? 3 
 __host__ __device__ constexpr int min_blocks(int K)
 {
     return K == 3 ? TS_FUSED_MIN_BLOCKS_K3 : K == 4 ? TS_FUSED_MIN_BLOCKS_K4 : TS_FUSED_MIN_BLOCKS;
+}
+
+// ... and of the multi-grid kernel
+__host__ __device__ constexpr int multi_min_blocks(int K)
+{
+    return K == 3   ? TS_FUSED_MULTI_MIN_BLOCKS_K3
+           : K == 4 ? TS_FUSED_MULTI_MIN_BLOCKS_K4
+                    : TS_FUSED_MIN_BLOCKS;
 }
 
 template <int K, int PP = 2, bool BRING = false>
@@ -926,7 +940,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
 // equal contiguous ranges, one per warp.  A grid's tensor maps live in its
 // descriptor in global memory, written once when the grid was set up.
 template <int K>
-__global__ void __launch_bounds__(Cfg<K>::WPC * 32, TS_FUSED_MIN_BLOCKS)
+__global__ void __launch_bounds__(Cfg<K>::WPC * 32, multi_min_blocks(K))
 fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t total_units,
                    int total_warps, int flip, int *err)
 {

@@ -65,6 +65,27 @@ def test_results_in_the_mix_equal_solo_runs():
         srv.close()
 
 
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_mix_equals_solo_at_each_depth(K):
+    """The server at depths 1-3 (graph-captured epochs and remainder
+    launches at every depth below K): each result equals its solo run at the
+    same depth bit for bit."""
+    items = _requests(6, seed=20 + K)
+    srv = trotter.Server(hbm_budget_bytes=8 << 30, max_slots=8, K=K, max_epoch_steps=10)
+    try:
+        tickets = [srv.submit(r.nx, r.ny, r.steps, r.dt, r.theta, V, re, im)
+                   for (r, re, im, V) in items]
+        for t in tickets:
+            assert srv.wait(t, 60000).status == 0
+        for (r, re, im, V), t in zip(items, tickets):
+            got = srv.fetch(t, r.ny, r.nx)
+            want = _solo(r, re, im, V, K=K)
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1]), r
+            srv.release(t)
+    finally:
+        srv.close()
+
+
 def test_admission_respects_the_budget():
     items = _requests(6, seed=3, sides=(256,), steps=(20, 40))
     per = trotter.ts_grid_layout(256, 256, trotter.TS_F32).slab_bytes
