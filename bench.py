@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--n3", type=int, default=512, help="side of the 3-D lattice in --variants")
+    ap.add_argument("--only", choices=["order4", "drive", "3d"], default=None,
+                    help="with --variants: run one variant (default depth) only")
     ap.add_argument("--variants", action="store_true",
                     help="time fourth-order steps and a time-dependent potential instead "
                          "(prints its own JSON line)")
@@ -571,7 +573,11 @@ def method_variants(args):
     runs = []
     cases = (("order 2", 2, 0, T, False), ("order 4", 4, 0, T4, False), ("order 4", 4, 3, T4, False),
              ("drive", 2, 0, T, True), ("drive", 2, 4, T, True))
+    only = args.only
     for name, order, K, steps, drive in cases:
+        if only and not (only == "order4" and order == 4 and K == 0 or
+                         only == "drive" and drive and K == 0):
+            continue
         ms = []
         for rep in range(max(1, args.steps) + 1):
             g.set_state(re0, im0)
@@ -597,6 +603,10 @@ def method_variants(args):
     g.close()
     del re0, im0, Vd, V1
     torch.cuda.empty_cache()
+    if only and only != "3d":
+        print(json.dumps({"metric": "site-steps/s of the method's variants", "n": n, "runs": runs,
+                          "data": "synthetic", "inputs": "resident in HBM"}), flush=True)
+        return 0
     # a 3-D lattice: n3^3 sites, separable packet and harmonic V built on the device
     n3 = args.n3
     t = torch.arange(n3, dtype=torch.float64, device="cuda")
@@ -611,7 +621,7 @@ def method_variants(args):
     V3 = (0.5e-4 * (r2[None, None, :] + r2[None, :, None] + r2[:, None, None])).contiguous()
     g3 = trotter.Grid(n3, n3, "f32", nz=n3)
     T3 = max(1, T // 4)
-    for path in ("fused", "plain"):
+    for path in ("fused",) if only else ("fused", "plain"):
         steps = T3 if path == "fused" else max(1, T3 // 10)
         ms = []
         for rep in range(max(1, args.steps) + 1):
