@@ -81,7 +81,10 @@ __device__ __forceinline__ void versine_short(float h, float &g, float &s)
     s = 2.0f * sh * ch;
 }
 
-__device__ __forceinline__ void versine_reduced(float h, float &g, float &s)
+// Kept out of line: large angles are rare, and inlining this path at every
+// use made the fused kernel's code outgrow the instruction cache.  Returns
+// (g, s) in registers.
+static __device__ __noinline__ float2 versine_reduced2(float h)
 {
     const float k = rintf(h * 0.318309886f);             // 1/pi
     float r = fmaf(-k, 3.140625f, h);                      // pi = A + B + C
@@ -101,8 +104,14 @@ __device__ __forceinline__ void versine_reduced(float h, float &g, float &s)
     pc = fmaf(t, pc, 1.0f / 24.0f);
     pc = fmaf(t, pc, -0.5f);
     const float ch = fmaf(t, pc, 1.0f);
-    g = 2.0f * sh * sh;
-    s = 2.0f * sh * ch;
+    return make_float2(2.0f * sh * sh, 2.0f * sh * ch);
+}
+
+__device__ __forceinline__ void versine_reduced(float h, float &g, float &s)
+{
+    const float2 r = versine_reduced2(h);
+    g = r.x;
+    s = r.y;
 }
 
 __device__ __forceinline__ void angle_versine(float phi, float &g, float &s)

@@ -111,12 +111,21 @@ zstream_kernel(const float *__restrict__ in_re, const float *__restrict__ in_im,
         win[k].re = make_float4(0.f, 0.f, 0.f, 0.f);
         win[k].im = win[k].re;
     }
+    // two slabs of loads in flight ahead of the one being swept
+    auto load = [&](int t, Col4 &c) {
+        c.re = *reinterpret_cast<const float4 *>(in_re + t * slab + col);
+        c.im = *reinterpret_cast<const float4 *>(in_im + t * slab + col);
+    };
+    Col4 nx0 = win[0], nx1 = win[0];
+    if (lo < hi) load(lo, nx0);
+    if (lo + 1 < hi) load(lo + 1, nx1);
     for (int t = lo; t < hi + M; ++t) {
 #pragma unroll
         for (int k = 0; k < M; ++k) win[k] = win[k + 1];
         if (t < hi) {
-            win[M].re = *reinterpret_cast<const float4 *>(in_re + t * slab + col);
-            win[M].im = *reinterpret_cast<const float4 *>(in_im + t * slab + col);
+            win[M] = nx0;
+            nx0 = nx1;
+            if (t + 2 < hi) load(t + 2, nx1);
         }
 #pragma unroll
         for (int i = 1; i <= M; ++i) {
@@ -167,12 +176,15 @@ cudaError_t launch_zstream(const float *in_re, const float *in_im, float *out_re
 {
     if (ny > 65535) return cudaErrorInvalidValue;
     const int chunks = (nx + 3) / 4;
-    dim3 grid((chunks + 127) / 128, ny, (nz + kZSeg - 1) / kZSeg);
+    // a block covers up to 128 column chunks of one row; narrower rows get
+    // narrower blocks rather than idle threads
+    const int threads = chunks >= 128 ? 128 : ((chunks + 31) / 32) * 32;
+    dim3 grid((chunks + threads - 1) / threads, ny, (nz + kZSeg - 1) / kZSeg);
     if (grid.z > 65535) return cudaErrorInvalidValue;
     if (q.m == 2)
-        zstream_kernel<2><<<grid, 128, 0, st>>>(in_re, in_im, out_re, out_im, nx, ny, nz, pitch, q);
+        zstream_kernel<2><<<grid, threads, 0, st>>>(in_re, in_im, out_re, out_im, nx, ny, nz, pitch, q);
     else if (q.m == 3)
-        zstream_kernel<3><<<grid, 128, 0, st>>>(in_re, in_im, out_re, out_im, nx, ny, nz, pitch, q);
+        zstream_kernel<3><<<grid, threads, 0, st>>>(in_re, in_im, out_re, out_im, nx, ny, nz, pitch, q);
     else
         return cudaErrorInvalidValue;
     count_launches(1);
