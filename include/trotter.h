@@ -93,7 +93,8 @@ ts_status ts_create_grid3(int64_t nx, int64_t ny, int64_t nz, ts_dtype dtype, vo
 /* Create a grid handle.  `slab` is a device pointer of at least
  * ts_grid_layout().slab_bytes bytes, 256-byte aligned, owned by the caller
  * (e.g. a torch tensor); pass NULL to have the library cudaMalloc (and later
- * free) its own slab.  The state starts at zero and the potential at V = 0
+ * free) its own slab.  The grid lives on the slab's device, which becomes the
+ * calling thread's current device.  The state starts at zero and the potential at V = 0
  * with dt = theta = 0 (identity step) until ts_set_potential is called.
  * Errors: TS_ERR_ARG (sizes, alignment, slab too small), TS_ERR_OOM,
  * TS_ERR_CUDA.  Syncs the device (allocation and zero-fill). */

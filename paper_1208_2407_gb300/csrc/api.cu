@@ -277,6 +277,20 @@ ts_status ts_create_grid3(int64_t nx, int64_t ny, int64_t nz, ts_dtype dtype, vo
         if (slab_bytes < L.slab_bytes)
             return fail(TS_ERR_ARG, "ts_create_grid: slab has %zu bytes, needs %zu", slab_bytes,
                         L.slab_bytes);
+        // The grid lives on the slab's device.  Making it current also binds
+        // its context to this thread, which the tensor-map encoding (a driver
+        // call) needs: a thread that has only used another runtime's cached
+        // streams and allocations may have none yet.
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, slab) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(TS_ERR_ARG, "ts_create_grid: slab is not device memory");
+        }
+        int cur = -1;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e == cudaSuccess && cur != pa.device) e = cudaSetDevice(pa.device);
+        if (e == cudaSuccess) e = cudaFree(nullptr);   // context current in this thread
+        if (e != cudaSuccess) return cuda_fail(e, "ts_create_grid: device of the slab");
     }
     bool owns = slab == nullptr;
     if (owns) {

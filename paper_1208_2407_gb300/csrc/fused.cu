@@ -1205,12 +1205,16 @@ bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int
     cuuint64_t strides[2] = {(cuuint64_t)(pitch * 4), (cuuint64_t)plane_bytes};
     cuuint32_t box[3] = {FUSED_BOX_COLS, FUSED_BOX_ROWS, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // (a driver call: the calling thread needs a current context)
+    const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base),
+                              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
-        *why = "cuTensorMapEncodeTiled rejected the plane layout";
+        thread_local char msg[96];
+        snprintf(msg, sizeof(msg), "cuTensorMapEncodeTiled rejected the plane layout (CUresult %d)",
+                 (int)r);
+        *why = msg;
         return false;
     }
     return true;
