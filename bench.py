@@ -322,6 +322,88 @@ def serve_bench(n_requests: int, seed: int, budget_gb: float = 120.0):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
+    """End to end through the C ABI with pinned host buffers.  Each step
+    uploads psi (FP32) and V (FP64) from pinned host memory, runs the step and
+    reads the state and the observables back.  Two grids on two streams,
+    driven by two host threads (the ctypes calls release the GIL), let one
+    grid's copies overlap the other's kernels -- double buffering through the
+    same public calls a user makes.  `log`, if a list, receives (thread, step,
+    start, set_state, set_potential, evolve, get_state, observe) times."""
+    import torch
+    from paper_1208_2407_gb300 import trotter
+    nbuf = 2
+    grids = [trotter.Grid(n, n, "f32") for _ in range(nbuf)]
+    # unequal priorities keep the two grids out of step: the first grid's
+    # kernels go first, and the second grid's copies overlap them (equal
+    # priorities measured 23.8 ms per step against 20.8 ms, kernels 19.3)
+    streams = [torch.cuda.Stream(priority=-1 if i == 0 else 0) for i in range(nbuf)]
+    h_re = torch.from_numpy(c["re"].astype(np.float32)).pin_memory()
+    h_im = torch.from_numpy(c["im"].astype(np.float32)).pin_memory()
+    h_V = torch.from_numpy(c["V"]).pin_memory()
+    outs = [(torch.empty((n, n), dtype=torch.float32).pin_memory(),
+             torch.empty((n, n), dtype=torch.float32).pin_memory()) for _ in range(nbuf)]
+    hp = lambda t: trotter._VP(t.data_ptr())
+    t_origin = [0.0]
+    # the host link's speed on this box (pinned, one 256 MiB copy each way)
+    probe = torch.empty(n * n, dtype=torch.float32, device="cuda")
+    link = {}
+    for name, dst, src in (("h2d_gbs", probe, h_re.view(-1)), ("d2h_gbs", outs[0][0].view(-1), probe)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dst.copy_(src, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        link[name] = round(4.0 * n * n / (a.elapsed_time(b) / 1e3) / 1e9, 1)
+    del probe
+
+    def e2e_steps(i, count):
+        gh, sp_i = grids[i].handle, trotter._VP(streams[i].cuda_stream)
+        o_re, o_im = outs[i]
+        for k in range(count):
+            t = [time.perf_counter()]
+            trotter.ts_set_state(gh, hp(h_re), hp(h_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
+            t.append(time.perf_counter())
+            trotter.ts_set_potential(gh, hp(h_V), trotter.TS_HOST, c["dt"], c["theta"], sp_i)
+            t.append(time.perf_counter())
+            trotter.ts_evolve(gh, T, K, sp_i)
+            t.append(time.perf_counter())
+            trotter.ts_get_state(gh, hp(o_re), hp(o_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
+            t.append(time.perf_counter())
+            trotter.ts_observe(gh, sp_i)
+            t.append(time.perf_counter())
+            if log is not None:
+                log.append((i, k, t[0] - t_origin[0]) + tuple(t[m + 1] - t[m] for m in range(5)))
+
+    def run_e2e(per_worker):
+        ths = [threading.Thread(target=e2e_steps, args=(i, per_worker)) for i in range(nbuf)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+
+    run_e2e(max(1, warmup // 2))
+    torch.cuda.synchronize()
+    dist.barrier()
+    per = max(1, (steps + nbuf - 1) // nbuf)
+    if log is not None:
+        log.clear()
+    t0 = t_origin[0] = time.perf_counter()
+    run_e2e(per)
+    torch.cuda.synchronize()
+    e2e_value = replica_throughput(dist, float(n) * n * T * per * nbuf, time.perf_counter() - t0)
+    for gg in grids:
+        gg.close()
+    return {"value": e2e_value, "unit": UNIT,
+            "h2d_bytes_per_step": int(n * n * (4 + 4 + 8)),
+            "d2h_bytes_per_step": int(n * n * (4 + 4) + 7 * 8),
+            "pipeline": "%d grids on %d streams (high and normal priority), one host "
+                        "thread each" % (nbuf, nbuf),
+            "steps": per * nbuf, "link": link}
+
+
 def run_ours(args):
     import torch
     from paper_1208_2407_gb300 import trotter
@@ -390,61 +472,11 @@ def run_ours(args):
     site_steps = float(n) * n * T
 
     # ---- end to end through the C ABI with pinned host buffers ----
-    # Each step uploads psi (FP32) and V (FP64) from pinned host memory, runs
-    # the step and reads the state and the observables back.  Two grids on two
-    # streams, driven by two host threads (the ctypes calls release the GIL),
-    # let one grid's copies overlap the other's kernels -- double buffering
-    # through the same public calls a user makes.
     e2e = None
     if not args.no_e2e:
         g.close()
         g = None
-        nbuf = 2
-        grids = [trotter.Grid(n, n, "f32") for _ in range(nbuf)]
-        # unequal priorities keep the two grids out of step: the first grid's
-        # kernels go first, and the second grid's copies overlap them (equal
-        # priorities measured 23.8 ms per step against 20.8 ms, kernels 19.3)
-        streams = [torch.cuda.Stream(priority=-1 if i == 0 else 0) for i in range(nbuf)]
-        h_re = torch.from_numpy(c["re"].astype(np.float32)).pin_memory()
-        h_im = torch.from_numpy(c["im"].astype(np.float32)).pin_memory()
-        h_V = torch.from_numpy(c["V"]).pin_memory()
-        outs = [(torch.empty((n, n), dtype=torch.float32).pin_memory(),
-                 torch.empty((n, n), dtype=torch.float32).pin_memory()) for _ in range(nbuf)]
-        hp = lambda t: trotter._VP(t.data_ptr())
-
-        def e2e_steps(i, count):
-            gh, sp_i = grids[i].handle, trotter._VP(streams[i].cuda_stream)
-            o_re, o_im = outs[i]
-            for _ in range(count):
-                trotter.ts_set_state(gh, hp(h_re), hp(h_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
-                trotter.ts_set_potential(gh, hp(h_V), trotter.TS_HOST, c["dt"], c["theta"], sp_i)
-                trotter.ts_evolve(gh, T, K, sp_i)
-                trotter.ts_get_state(gh, hp(o_re), hp(o_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
-                trotter.ts_observe(gh, sp_i)
-
-        def run_e2e(per_worker):
-            ths = [threading.Thread(target=e2e_steps, args=(i, per_worker)) for i in range(nbuf)]
-            for t in ths:
-                t.start()
-            for t in ths:
-                t.join()
-
-        run_e2e(max(1, args.warmup // 2))
-        torch.cuda.synchronize()
-        dist.barrier()
-        per = max(1, (args.steps + nbuf - 1) // nbuf)
-        t0 = time.perf_counter()
-        run_e2e(per)
-        torch.cuda.synchronize()
-        e2e_value = replica_throughput(dist, site_steps * per * nbuf, time.perf_counter() - t0)
-        e2e = {"value": e2e_value, "unit": UNIT,
-               "h2d_bytes_per_step": int(n * n * (4 + 4 + 8)),
-               "d2h_bytes_per_step": int(n * n * (4 + 4) + 7 * 8),
-               "pipeline": "%d grids on %d streams (high and normal priority), one host "
-                           "thread each" % (nbuf, nbuf),
-               "steps": per * nbuf}
-        for gg in grids:
-            gg.close()
+        e2e = e2e_bench(c, n, T, K, args.steps, args.warmup, dist)
 
     # ---- roofline of the dominant kernel (the fused K-step kernel) ----
     peaks = {}
