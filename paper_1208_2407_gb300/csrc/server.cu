@@ -99,6 +99,7 @@ constexpr int kTables = 32;
 struct ts_server {
     ts_server_cfg cfg{};
     int K = 4, L_max = 8;
+    int device = 0;                 // the creating thread's device; the worker runs there
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::unordered_map<uint64_t, ReqP> reqs;
@@ -370,6 +371,7 @@ void ts_server::enqueue_epoch(std::unique_lock<std::mutex> &lk)
 
 void ts_server::run()
 {
+    cudaSetDevice(device);   // a new thread starts on device 0 otherwise
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
         // retire finished epochs
@@ -467,6 +469,7 @@ ts_status ts_server_create(const ts_server_cfg *cfg, ts_server **out)
     if (!s) return err(TS_ERR_OOM, "ts_server_create: host allocation failed");
     s->cfg = *cfg;
     s->K = cfg->K == 0 ? 4 : cfg->K;
+    cudaGetDevice(&s->device);
     const int steps_per_epoch = cfg->max_epoch_steps > 0 ? cfg->max_epoch_steps : 32;
     s->L_max = std::max(1, steps_per_epoch / s->K);
     cudaError_t e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
