@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "ffloat.cuh"
 #include "internal.h"
+#include "walk.cuh"
 
 namespace ts {
 
@@ -27,27 +28,62 @@ inline int grid_for(int64_t work, int per_block)
     return (int)b;
 }
 
-template <typename Ts, typename Td>
-__global__ void convert_in_kernel(const Ts *__restrict__ src, Td *__restrict__ dst, int nx,
-                                  int ny, int64_t pitch)
+// Dense (nx per row) <-> pitched conversions, one row per blockIdx.y step.
+// When nx is a multiple of 4 every row starts 16-byte aligned in both
+// layouts, and each thread moves 4 elements with vector accesses.
+template <typename T>
+struct Quad {
+    T v[4];
+};
+
+template <typename T>
+__device__ __forceinline__ Quad<T> load4(const T *p)
 {
-    const int64_t n = (int64_t)nx * ny;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t y = i / nx, x = i - y * nx;
-        dst[y * pitch + x] = (Td)src[i];
+    Quad<T> q;
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        q.v[0] = a.x; q.v[1] = a.y; q.v[2] = a.z; q.v[3] = a.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        q.v[0] = a.x; q.v[1] = a.y; q.v[2] = b.x; q.v[3] = b.y;
+    }
+    return q;
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T *p, const T (&v)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
     }
 }
 
-template <typename Ts, typename Td>
-__global__ void convert_out_kernel(const Ts *__restrict__ src, Td *__restrict__ dst, int nx,
-                                   int ny, int64_t pitch)
+// IN: dense src -> pitched dst; otherwise pitched src -> dense dst
+template <bool IN, typename Ts, typename Td>
+__global__ void convert_kernel(const Ts *__restrict__ src, Td *__restrict__ dst, int nx, int ny,
+                               int64_t pitch, bool vec4)
 {
-    const int64_t n = (int64_t)nx * ny;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t y = i / nx, x = i - y * nx;
-        dst[i] = (Td)src[y * pitch + x];
+    for (int64_t y = blockIdx.y; y < ny; y += gridDim.y) {
+        const Ts *s = src + y * (IN ? (int64_t)nx : pitch);
+        Td *d = dst + y * (IN ? pitch : (int64_t)nx);
+        if (vec4) {
+            for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nx / 4;
+                 q += gridDim.x * blockDim.x) {
+                const Quad<Ts> a = load4(s + 4 * q);
+                Td b[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) b[k] = (Td)a.v[k];
+                store4(d + 4 * q, b);
+            }
+        } else {
+            for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx;
+                 x += gridDim.x * blockDim.x)
+                d[x] = (Td)s[x];
+        }
     }
 }
 
@@ -60,9 +96,10 @@ __global__ void phase_table_kernel(const double *__restrict__ V, T *__restrict__
                                    int64_t pitch, double dt)
 {
     const int64_t n = (int64_t)nx * ny;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t y = i / nx, x = i - y * nx;
+    for (Walk w(nx, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                (int64_t)gridDim.x * blockDim.x);
+         w.i < n; w.next()) {
+        const int64_t i = w.i, y = w.y, x = w.x;
         double v = V[i];
         double ph = v * dt;
         double sh = sin(0.5 * ph);
@@ -150,10 +187,10 @@ __global__ void phase_table_f32_kernel(const double *__restrict__ V, float *__re
     for (int i = threadIdx.x; i < 256; i += blockDim.x) sc[i] = tab.sc[i];
     __syncthreads();
     const int64_t n = (int64_t)nx * ny;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t y = i / nx, x = i - y * nx;
-        const int64_t j = y * pitch + x;
+    for (Walk w(nx, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                (int64_t)gridDim.x * blockDim.x);
+         w.i < n; w.next()) {
+        const int64_t i = w.i, j = w.y * pitch + w.x;
         const double v = V[i];
         float vh, vl;
         int S;
@@ -296,36 +333,34 @@ inline dim3 grid2d(int64_t per_row, int rows)
 
 }  // namespace
 
+template <bool IN>
+cudaError_t launch_convert(const void *src, bool src_f64, void *dst, bool dst_f64, int nx, int ny,
+                           int64_t pitch, cudaStream_t st)
+{
+    const bool vec4 = (nx % 4) == 0 && ((uintptr_t)src % 16) == 0 && ((uintptr_t)dst % 16) == 0;
+    dim3 grid = grid2d(vec4 ? nx / 4 : nx, ny);
+    if (src_f64 && dst_f64)
+        convert_kernel<IN, double, double><<<grid, kThreads, 0, st>>>((const double *)src, (double *)dst, nx, ny, pitch, vec4);
+    else if (src_f64)
+        convert_kernel<IN, double, float><<<grid, kThreads, 0, st>>>((const double *)src, (float *)dst, nx, ny, pitch, vec4);
+    else if (dst_f64)
+        convert_kernel<IN, float, double><<<grid, kThreads, 0, st>>>((const float *)src, (double *)dst, nx, ny, pitch, vec4);
+    else
+        convert_kernel<IN, float, float><<<grid, kThreads, 0, st>>>((const float *)src, (float *)dst, nx, ny, pitch, vec4);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_convert_in(const void *src, bool src_f64, void *dst, bool dst_f64, int nx,
                               int ny, int64_t pitch, cudaStream_t st)
 {
-    int grid = grid_for((int64_t)nx * ny, kThreads);
-    if (src_f64 && dst_f64)
-        convert_in_kernel<double, double><<<grid, kThreads, 0, st>>>((const double *)src, (double *)dst, nx, ny, pitch);
-    else if (src_f64)
-        convert_in_kernel<double, float><<<grid, kThreads, 0, st>>>((const double *)src, (float *)dst, nx, ny, pitch);
-    else if (dst_f64)
-        convert_in_kernel<float, double><<<grid, kThreads, 0, st>>>((const float *)src, (double *)dst, nx, ny, pitch);
-    else
-        convert_in_kernel<float, float><<<grid, kThreads, 0, st>>>((const float *)src, (float *)dst, nx, ny, pitch);
-    count_launches(1);
-    return cudaGetLastError();
+    return launch_convert<true>(src, src_f64, dst, dst_f64, nx, ny, pitch, st);
 }
 
 cudaError_t launch_convert_out(const void *src, bool src_f64, void *dst, bool dst_f64, int nx,
                                int ny, int64_t pitch, cudaStream_t st)
 {
-    int grid = grid_for((int64_t)nx * ny, kThreads);
-    if (src_f64 && dst_f64)
-        convert_out_kernel<double, double><<<grid, kThreads, 0, st>>>((const double *)src, (double *)dst, nx, ny, pitch);
-    else if (src_f64)
-        convert_out_kernel<double, float><<<grid, kThreads, 0, st>>>((const double *)src, (float *)dst, nx, ny, pitch);
-    else if (dst_f64)
-        convert_out_kernel<float, double><<<grid, kThreads, 0, st>>>((const float *)src, (double *)dst, nx, ny, pitch);
-    else
-        convert_out_kernel<float, float><<<grid, kThreads, 0, st>>>((const float *)src, (float *)dst, nx, ny, pitch);
-    count_launches(1);
-    return cudaGetLastError();
+    return launch_convert<false>(src, src_f64, dst, dst_f64, nx, ny, pitch, st);
 }
 
 cudaError_t launch_phase_table(const double *V, void *pg, void *ps, void *vplane, bool f64, int nx,

@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "ffloat.cuh"
 #include "internal.h"
+#include "walk.cuh"
 
 namespace ts {
 
@@ -95,10 +96,11 @@ observe_f32_kernel(const float *__restrict__ re, const float *__restrict__ im,
 
     const int chunks_per_row = (nx + 3) / 4;
     const int64_t nchunks = (int64_t)chunks_per_row * ny;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(c / chunks_per_row);
-        const int x0 = (int)(c - (int64_t)y * chunks_per_row) * 4;
+    for (Walk w(chunks_per_row, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                (int64_t)gridDim.x * blockDim.x);
+         w.i < nchunks; w.next()) {
+        const int y = (int)w.y;
+        const int x0 = (int)w.x * 4;
         const int64_t o = (int64_t)y * pitch + x0;
         const float4 r4 = *reinterpret_cast<const float4 *>(re + o);
         const float4 m4 = *reinterpret_cast<const float4 *>(im + o);
@@ -180,10 +182,11 @@ inner_f32_kernel(const float *__restrict__ ar, const float *__restrict__ ai,
     FF sr = ff_make(0.f), si = ff_make(0.f);
     const int chunks_per_row = (nx + 3) / 4;
     const int64_t nchunks = (int64_t)chunks_per_row * ny;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(c / chunks_per_row);
-        const int x0 = (int)(c - (int64_t)y * chunks_per_row) * 4;
+    for (Walk w(chunks_per_row, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                (int64_t)gridDim.x * blockDim.x);
+         w.i < nchunks; w.next()) {
+        const int y = (int)w.y;
+        const int x0 = (int)w.x * 4;
         const int64_t o = (int64_t)y * pitch + x0;
         const float4 a4 = *reinterpret_cast<const float4 *>(ar + o);
         const float4 b4 = *reinterpret_cast<const float4 *>(ai + o);
@@ -221,10 +224,11 @@ observe_kernel(const T *__restrict__ re, const T *__restrict__ im, const T *__re
 
     const int chunks_per_row = (nx + 3) / 4;
     const int64_t nchunks = (int64_t)chunks_per_row * ny;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(c / chunks_per_row);
-        const int x0 = (int)(c - (int64_t)y * chunks_per_row) * 4;
+    for (Walk w(chunks_per_row, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                (int64_t)gridDim.x * blockDim.x);
+         w.i < nchunks; w.next()) {
+        const int y = (int)w.y;
+        const int x0 = (int)w.x * 4;
         const int64_t o = (int64_t)y * pitch;
         double run[NQ];
 #pragma unroll
@@ -306,10 +310,11 @@ observe3_kernel(const T *__restrict__ re, const T *__restrict__ im, const T *__r
     const int64_t slab = (int64_t)ny * pitch;
     const int chunks_per_row = (nx + 3) / 4;
     const int64_t nchunks = (int64_t)chunks_per_row * rows;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = c / chunks_per_row;
-        const int x0 = (int)(c - r * chunks_per_row) * 4;
+    for (Walk w(chunks_per_row, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                (int64_t)gridDim.x * blockDim.x);
+         w.i < nchunks; w.next()) {
+        const int64_t r = w.y;
+        const int x0 = (int)w.x * 4;
         const int z = (int)(r / ny), y = (int)(r - (int64_t)z * ny);
         const int64_t o = r * pitch;
         double run[NQ];
