@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the FP32 / FP64 path comparison")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--n3", type=int, default=512, help="side of the 3-D lattice in --variants")
     ap.add_argument("--only", choices=["order4", "drive", "3d"], default=None,
@@ -404,6 +406,45 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
             "steps": per * nbuf, "link": link}
 
 
+def precision_paths(c, n, fused_rate, reps=3, steps=10):
+    """FP32 vs FP64 on the same workload, inputs resident in HBM: Trotter
+    site-steps/s of ts_evolve and of the plain one-sweep-per-kernel path
+    (ts_evolve_plain, nine launches per step) for each precision, median of
+    `reps` runs of `steps` steps timed with CUDA events.  FP64 grids run one
+    sweep per launch under ts_evolve too, with the sweeps merged where steps
+    meet (6 n + 2 sweeps) in lifting form."""
+    import torch
+    from paper_1208_2407_gb300 import trotter
+    out = {"steps": steps, "fp32_fused": fused_rate}
+    for dtype in ("f32", "f64"):
+        tdt = torch.float32 if dtype == "f32" else torch.float64
+        g = trotter.Grid(n, n, dtype)
+        try:
+            g.set_state(torch.from_numpy(c["re"]).to(tdt).cuda(),
+                        torch.from_numpy(c["im"]).to(tdt).cuda())
+            g.set_potential(torch.from_numpy(c["V"]).cuda(), c["dt"], c["theta"])
+            runs = [("plain", g.evolve_plain)] + ([("default", g.evolve)] if dtype == "f64" else [])
+            for name, fn in runs:
+                fn(1)
+                rates = []
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    fn(steps)
+                    b.record()
+                    torch.cuda.synchronize()
+                    rates.append(float(n) * n * steps / (a.elapsed_time(b) / 1e3))
+                out["%s_%s" % ("fp32" if dtype == "f32" else "fp64", name)] = \
+                    sorted(rates)[len(rates) // 2]
+        finally:
+            g.close()
+    out["fp32_fused_over_fp64_plain"] = fused_rate / out["fp64_plain"]
+    out["fp32_fused_over_fp64_default"] = fused_rate / out["fp64_default"]
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_1208_2407_gb300 import trotter
@@ -495,6 +536,13 @@ def run_ours(args):
                 "avg_launch_ms": avg_launch_ms,
                 "algorithmic_bytes_per_launch": BYTES_PER_SITE_LAUNCH * n * n}
 
+    precision = None
+    if rank == 0 and not args.no_precision:
+        if g is not None:
+            g.close()
+            g = None
+        precision = precision_paths(c, n, site_steps * args.steps / (evolve_ms / 1e3))
+
     serve = None
     if rank == 0 and not args.no_serve:
         if g is not None:
@@ -524,6 +572,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "obs_last": {"norm": obs["norm"], "energy": obs["e_kin"] + obs["e_pot"]},
+            "precision": precision,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)
@@ -547,7 +596,7 @@ def paper_sizes(args):
     trotter.load()
     out = []
     for L, dtype, path in ((24576, "f32", "fused"), (24576, "f32", "plain"),
-                           (17472, "f64", "plain")):
+                           (17472, "f64", "evolve"), (17472, "f64", "plain")):
         tdt = torch.float32 if dtype == "f32" else torch.float64
         x = torch.arange(L, device="cuda", dtype=torch.float64)
         sigma, k = L / 16.0, 0.5
@@ -562,7 +611,8 @@ def paper_sizes(args):
         g.set_potential(V, 0.05, 0.025)
         del re, im, V
         torch.cuda.empty_cache()
-        run = (lambda n: g.evolve(n)) if path == "fused" else (lambda n: g.evolve_plain(n))
+        # "evolve": ts_evolve on an FP64 grid (one sweep per launch, merged)
+        run = (lambda n: g.evolve_plain(n)) if path == "plain" else (lambda n: g.evolve(n))
         run(1)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

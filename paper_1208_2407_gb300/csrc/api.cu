@@ -649,6 +649,74 @@ ts_status plain_run(ts_grid *g, int64_t steps, const ts::RotCoef &c, const void 
 
 
 
+// FP64 grids (ts_evolve): second-order substeps one sweep per launch, with
+// the sweeps merged where two substeps meet.  X, Y (and Z) factors act on
+// different coordinates and commute, and two factors of one family add
+// their angles, so the mirror half of substep i and the first half of
+// substep i + 1,
+//   [Yo Ye Xo Xe](i) [Xe Xo Ye Yo](i+1)  (plus Zo Ze / Ze Zo in 3-D),
+// equal Xo(i) Xe(i + i+1) Xo(i+1) . Yo(i) Ye(i + i+1) Yo(i+1) [. Z]: three
+// sweeps per axis instead of four.  A sweep at angle phi uses the lifting
+// form (tan(phi/2), sin phi; 3 FMA per site instead of 4) when |phi| <= pi/2,
+// the versine form otherwise.  Substep i is sub(i) = {kinetic half angle,
+// phase table, drive angle or 0 with has_drive false}.
+struct Substep {
+    double theta;
+    const void *pg, *ps;
+    bool has_drive;
+    double adt;
+};
+
+extern "C++" {
+template <typename SubAt>
+ts_status merged_run(ts_grid *g, int64_t n, SubAt sub, cudaStream_t st)
+{
+    if (n <= 0) return TS_OK;
+    const int nx = (int)g->L.nx, ny = (int)g->rows();
+    const int sy = (int)g->L.ny, sz = (int)g->L.nz;
+    const int64_t pitch = g->L.pitch;
+    void *re = g->re(), *im = g->im();
+    const int n_axes = g->is3d() ? 3 : 2;
+    auto sweep = [&](int axis, int parity, double phi) {
+        const bool lift = std::fabs(phi) <= 0.5 * M_PI;
+        const double h = std::sin(0.5 * phi);
+        const double c = lift ? std::tan(0.5 * phi) : 2.0 * h * h, s = std::sin(phi);
+        if (axis == 0 || !g->is3d())
+            return ts::launch_plain_sweep(re, im, true, nx, ny, pitch, axis, parity, c, s, st, lift);
+        if (axis == 1)
+            return ts::launch_plain_sweep_y3(re, im, true, nx, sy, sz, pitch, parity, c, s, st, lift);
+        return ts::launch_plain_sweep_z(re, im, true, nx, sy, sz, pitch, parity, c, s, st, lift);
+    };
+    Substep cur = sub(0);
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < n_axes && e == cudaSuccess; ++a) {
+        e = sweep(a, 0, cur.theta);
+        if (e == cudaSuccess) e = sweep(a, 1, cur.theta);
+    }
+    for (int64_t i = 0; i < n && e == cudaSuccess; ++i) {
+        e = ts::launch_plain_phase(re, im, cur.pg, cur.ps, true, nx, ny, pitch, st);
+        if (e == cudaSuccess && cur.has_drive)
+            e = ts::launch_plain_drive(re, im, g->drive_v1(), true, nx, ny, pitch, cur.adt, st);
+        if (i + 1 < n) {
+            const Substep next = sub(i + 1);
+            for (int a = 0; a < n_axes && e == cudaSuccess; ++a) {
+                e = sweep(a, 1, cur.theta);
+                if (e == cudaSuccess) e = sweep(a, 0, cur.theta + next.theta);
+                if (e == cudaSuccess) e = sweep(a, 1, next.theta);
+            }
+            cur = next;
+        } else {
+            for (int a = n_axes - 1; a >= 0 && e == cudaSuccess; --a) {
+                e = sweep(a, 1, cur.theta);
+                if (e == cudaSuccess) e = sweep(a, 0, cur.theta);
+            }
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "FP64 sweep launch");
+    return TS_OK;
+}
+}  // extern "C++"
+
 // `steps` second-order steps on the fused path at depth K (a remainder runs
 // at a smaller depth), with the coefficients c and the phase table map tm.
 ts_status fused_run(ts_grid *g, int64_t steps, int K, const ts::RotCoef &c,
@@ -735,8 +803,8 @@ ts_status evolve3_fused(ts_grid *g, int64_t steps, cudaStream_t st)
 }
 
 // Steps with the time-dependent potential V0 + a_n V1: the next `steps`
-// amplitudes, each multiplied by dt; the fused kernel at depth <= 4 or,
-// for FP64 grids and |theta| > pi/4, the plain path.
+// amplitudes, each multiplied by dt; the fused kernel at depth <= 4 or, for
+// ts_evolve_plain and FP32 grids with |theta| > pi/4, the plain path.
 ts_status evolve_driven(ts_grid *g, int64_t steps, int K, bool plain, cudaStream_t st)
 {
     const int64_t left = (int64_t)g->drive_a.size() - g->drive_pos;
@@ -824,6 +892,34 @@ ts_status evolve4(ts_grid *g, int64_t steps, int K, bool plain, cudaStream_t st)
     return s;
 }
 
+// ts_evolve on FP64 grids: the merged sweep sequence for every kind of step
+// (second order, 3-D, fourth order, time-dependent potential).
+ts_status evolve_f64(ts_grid *g, int64_t steps, cudaStream_t st)
+{
+    if (g->driven) {
+        const int64_t left = (int64_t)g->drive_a.size() - g->drive_pos;
+        if (steps > left)
+            return fail(TS_ERR_ARG,
+                        "ts_evolve: %lld steps asked for but %lld drive amplitudes are left",
+                        (long long)steps, (long long)left);
+        const int64_t pos = g->drive_pos;
+        ts_status s = merged_run(g, steps, [&](int64_t i) {
+            return Substep{g->theta, g->pg(), g->ps(), true,
+                           g->drive_a[(size_t)(pos + i)] * g->dt};
+        }, st);
+        if (s == TS_OK) g->drive_pos += steps;
+        return s;
+    }
+    if (g->order == 4) {   // substeps a a b a a per step
+        const double p4 = 1.0 / (4.0 - std::cbrt(4.0));
+        const Substep a = {p4 * g->theta, g->pg(), g->ps(), false, 0.0};
+        const Substep b = {(1.0 - 4.0 * p4) * g->theta, g->pg_b(), g->ps_b(), false, 0.0};
+        return merged_run(g, 5 * steps, [&](int64_t i) { return i % 5 == 2 ? b : a; }, st);
+    }
+    const Substep u = {g->theta, g->pg(), g->ps(), false, 0.0};
+    return merged_run(g, steps, [&](int64_t) { return u; }, st);
+}
+
 }  // namespace
 
 ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
@@ -833,22 +929,24 @@ ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
     if (K < 0 || K > ts::FUSED_MAX_K) return fail(TS_ERR_ARG, "ts_evolve: K must be in [0, 8]");
     if (steps == 0) return TS_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    if (g->f64() && K != 0)
-        return fail(TS_ERR_UNSUPPORTED, "ts_evolve: FP64 grids run the plain path (K must be 0)");
+    if (g->f64()) {
+        if (K != 0)
+            return fail(TS_ERR_UNSUPPORTED,
+                        "ts_evolve: FP64 grids run one sweep per launch (K must be 0)");
+        return evolve_f64(g, steps, st);
+    }
     if (g->is3d()) {
-        if (g->f64() || std::fabs(g->theta) > 0.25 * M_PI || (g->L.ny & 1) || g->L.ny > 65535)
+        if (std::fabs(g->theta) > 0.25 * M_PI || (g->L.ny & 1) || g->L.ny > 65535)
             return plain_steps(g, steps, st);
         return evolve3_fused(g, steps, st);
     }
-    if (g->driven)
-        return evolve_driven(g, steps, K, g->f64() || std::fabs(g->theta) > 0.25 * M_PI, st);
+    if (g->driven) return evolve_driven(g, steps, K, std::fabs(g->theta) > 0.25 * M_PI, st);
     if (g->order == 4) {
         // the substep angles p theta and (1-4p) theta must both suit the fused kernel
         const double p4 = 1.0 / (4.0 - std::cbrt(4.0));
-        const bool plain = g->f64() || std::fabs(g->theta) * std::fabs(1.0 - 4.0 * p4) > 0.25 * M_PI;
+        const bool plain = std::fabs(g->theta) * std::fabs(1.0 - 4.0 * p4) > 0.25 * M_PI;
         return evolve4(g, steps, K, plain, st);
     }
-    if (g->f64()) return plain_steps(g, steps, st);
     // The fused kernel applies the rotations at theta and 2 theta as three
     // shears with tan(theta/2) and tan(theta); it requires |theta| <= pi/4
     // (|2 theta| <= pi/2).  Larger angles -- far beyond any useful Trotter

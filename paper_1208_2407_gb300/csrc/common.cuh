@@ -2,11 +2,13 @@
 //
 // Rotation convention (Sec. 2, the block exponential M with hopping -J):
 //   a' = cos(t) a + i sin(t) b,  b' = i sin(t) a + cos(t) b.
-// Every kernel applies it in the versine form
-//   a' = a - g a + i s b,  g = 1 - cos(t) = 2 sin^2(t/2),  s = sin(t),
-// with (g, s) computed in FP64 and rounded once, so that the per-sweep
-// unitarity defect of the rounded coefficients is O(ulp * t) rather than
-// O(ulp): the error of (1 - g)^2 + s^2 - 1 stays ~1e-10 in FP32.
+// The kernels apply it in one of two forms, never with cos(t) itself:
+//  - the versine form a' = a - g a + i s b, g = 1 - cos(t) = 2 sin^2(t/2),
+//    s = sin(t), with (g, s) computed in FP64 and rounded once, so that the
+//    per-sweep unitarity defect of the rounded coefficients is O(ulp * t)
+//    rather than O(ulp): (1 - g)^2 + s^2 - 1 stays ~1e-10 in FP32;
+//  - the lifting form (three shears with tan(t/2) and sin(t), each of
+//    determinant 1) where both members of a pair are at hand and |t| <= pi/2.
 #pragma once
 
 #include <cstdint>
@@ -46,6 +48,29 @@ __device__ __forceinline__ void rot_lift(float &ar, float &ai, float &br, float 
     ai = fmaf(s, br, ai);
     ar = fmaf(-t, bi, ar);
     br = fmaf(-t, ai, br);
+}
+
+// The same in FP64.
+__device__ __forceinline__ void rot_lift(double &ar, double &ai, double &br, double &bi, double t,
+                                         double s)
+{
+    ar = fma(-t, bi, ar);
+    br = fma(-t, ai, br);
+    bi = fma(s, ar, bi);
+    ai = fma(s, br, ai);
+    ar = fma(-t, bi, ar);
+    br = fma(-t, ai, br);
+}
+
+// A pair rotation in lifting form (c = tan(theta/2)) or versine form
+// (c = 1 - cos(theta)); s = sin(theta) in both.
+template <bool LIFT, typename T>
+__device__ __forceinline__ void rot_pair(T &ar, T &ai, T &br, T &bi, T c, T s)
+{
+    if constexpr (LIFT)
+        rot_lift(ar, ai, br, bi, c, s);
+    else
+        rot2(ar, ai, br, bi, c, s);
 }
 
 // psi <- psi * exp(-i phi) with g = 1 - cos(phi), s = sin(phi):

@@ -29,9 +29,11 @@ cudaError_t launch_convert_out(const void *src, bool src_f64, void *dst, bool ds
 // V (dense FP64) -> (gamma_V, s_V, V) pitched planes of the grid's type
 cudaError_t launch_phase_table(const double *V, void *pg, void *ps, void *vplane, bool f64,
                                int nx, int ny, int64_t pitch, double dt, cudaStream_t st);
-// one sweep along x (axis 0) or y (axis 1) of the given parity, in place
+// one sweep along x (axis 0) or y (axis 1) of the given parity, in place;
+// (g, s) versine coefficients, or with lift (FP64 only) (tan(theta/2), s)
 cudaError_t launch_plain_sweep(void *re, void *im, bool f64, int nx, int ny, int64_t pitch,
-                               int axis, int parity, double g, double s, cudaStream_t st);
+                               int axis, int parity, double g, double s, cudaStream_t st,
+                               bool lift = false);
 // the diagonal phase exp(-i V dt) from the stored table, in place
 cudaError_t launch_plain_phase(void *re, void *im, const void *pg, const void *ps, bool f64,
                                int nx, int ny, int64_t pitch, cudaStream_t st);
@@ -48,10 +50,11 @@ cudaError_t launch_plain_drive(void *re, void *im, const void *v1, bool f64, int
 // counted from the slab's first row), in place.
 cudaError_t launch_plain_sweep_y3(void *re, void *im, bool f64, int nx, int ny, int nz,
                                   int64_t pitch, int parity, double g, double s,
-                                  cudaStream_t st);
+                                  cudaStream_t st, bool lift = false);
 // One Z sweep: pairs of slabs (z, z+1), z of the given parity, in place.
 cudaError_t launch_plain_sweep_z(void *re, void *im, bool f64, int nx, int ny, int nz,
-                                 int64_t pitch, int parity, double g, double s, cudaStream_t st);
+                                 int64_t pitch, int parity, double g, double s, cudaStream_t st,
+                                 bool lift = false);
 // Up to three Z sweeps applied in one streaming pass over an FP32 grid,
 // from the planes (in_re, in_im) to (out_re, out_im): sweep i pairs slabs
 // (z, z+1) with z % 2 == parity[i], in lifting form (t[i], s[i]).

@@ -22,7 +22,8 @@ inline dim3 grid2d(int64_t per_row, int64_t rows)
 }
 
 // Y pairs (y, y+1) inside every slab: index q over nz * pairs-per-slab.
-template <typename T>
+// (g, s) are the versine coefficients, or with LIFT (t, s) of the lifting form.
+template <typename T, bool LIFT = false>
 __global__ void sweep_y3_kernel(T *__restrict__ re, T *__restrict__ im, int nx, int ny, int nz,
                                 int64_t pitch, int parity, T g, T s)
 {
@@ -35,7 +36,7 @@ __global__ void sweep_y3_kernel(T *__restrict__ re, T *__restrict__ im, int nx, 
         T *r1 = r0 + pitch, *m1 = m0 + pitch;
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
             T ar = r0[x], ai = m0[x], br = r1[x], bi = m1[x];
-            rot2(ar, ai, br, bi, g, s);
+            rot_pair<LIFT>(ar, ai, br, bi, g, s);
             r0[x] = ar;
             m0[x] = ai;
             r1[x] = br;
@@ -45,7 +46,7 @@ __global__ void sweep_y3_kernel(T *__restrict__ re, T *__restrict__ im, int nx, 
 }
 
 // Z pairs (z, z+1): index q over pairs-of-slabs * ny rows.
-template <typename T>
+template <typename T, bool LIFT = false>
 __global__ void sweep_z_kernel(T *__restrict__ re, T *__restrict__ im, int nx, int ny, int nz,
                                int64_t pitch, int parity, T g, T s)
 {
@@ -59,7 +60,7 @@ __global__ void sweep_z_kernel(T *__restrict__ re, T *__restrict__ im, int nx, i
         T *r1 = r0 + slab, *m1 = m0 + slab;
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
             T ar = r0[x], ai = m0[x], br = r1[x], bi = m1[x];
-            rot2(ar, ai, br, bi, g, s);
+            rot_pair<LIFT>(ar, ai, br, bi, g, s);
             r0[x] = ar;
             m0[x] = ai;
             r1[x] = br;
@@ -144,12 +145,15 @@ zstream_kernel(const float *__restrict__ in_re, const float *__restrict__ in_im,
 }  // namespace
 
 cudaError_t launch_plain_sweep_y3(void *re, void *im, bool f64, int nx, int ny, int nz,
-                                  int64_t pitch, int parity, double g, double s, cudaStream_t st)
+                                  int64_t pitch, int parity, double g, double s, cudaStream_t st,
+                                  bool lift)
 {
     const int64_t npairs = (int64_t)((ny - parity) / 2) * nz;
     if (npairs <= 0) return cudaSuccess;
     dim3 grid = grid2d(nx, npairs);
-    if (f64)
+    if (f64 && lift)
+        sweep_y3_kernel<double, true><<<grid, kThreads, 0, st>>>((double *)re, (double *)im, nx, ny, nz, pitch, parity, g, s);
+    else if (f64)
         sweep_y3_kernel<double><<<grid, kThreads, 0, st>>>((double *)re, (double *)im, nx, ny, nz, pitch, parity, g, s);
     else
         sweep_y3_kernel<float><<<grid, kThreads, 0, st>>>((float *)re, (float *)im, nx, ny, nz, pitch, parity, (float)g, (float)s);
@@ -158,12 +162,15 @@ cudaError_t launch_plain_sweep_y3(void *re, void *im, bool f64, int nx, int ny, 
 }
 
 cudaError_t launch_plain_sweep_z(void *re, void *im, bool f64, int nx, int ny, int nz,
-                                 int64_t pitch, int parity, double g, double s, cudaStream_t st)
+                                 int64_t pitch, int parity, double g, double s, cudaStream_t st,
+                                 bool lift)
 {
     const int64_t nrows = (int64_t)((nz - parity) / 2) * ny;
     if (nrows <= 0) return cudaSuccess;
     dim3 grid = grid2d(nx, nrows);
-    if (f64)
+    if (f64 && lift)
+        sweep_z_kernel<double, true><<<grid, kThreads, 0, st>>>((double *)re, (double *)im, nx, ny, nz, pitch, parity, g, s);
+    else if (f64)
         sweep_z_kernel<double><<<grid, kThreads, 0, st>>>((double *)re, (double *)im, nx, ny, nz, pitch, parity, g, s);
     else
         sweep_z_kernel<float><<<grid, kThreads, 0, st>>>((float *)re, (float *)im, nx, ny, nz, pitch, parity, (float)g, (float)s);

@@ -244,7 +244,8 @@ __global__ void phase_table_f32_kernel(const double *__restrict__ V, float *__re
 }
 
 // X sweep: pairs (x, x+1), x = parity + 2p, every row; one thread per pair.
-template <typename T>
+// (g, s) are the versine coefficients, or with LIFT (t, s) of the lifting form.
+template <typename T, bool LIFT = false>
 __global__ void plain_sweep_x_kernel(T *__restrict__ re, T *__restrict__ im, int nx, int ny,
                                      int64_t pitch, int parity, T g, T s)
 {
@@ -257,7 +258,7 @@ __global__ void plain_sweep_x_kernel(T *__restrict__ re, T *__restrict__ im, int
              p += gridDim.x * blockDim.x) {
             int x = parity + 2 * p;
             T ar = r[x], ai = m[x], br = r[x + 1], bi = m[x + 1];
-            rot2(ar, ai, br, bi, g, s);
+            rot_pair<LIFT>(ar, ai, br, bi, g, s);
             r[x] = ar;
             m[x] = ai;
             r[x + 1] = br;
@@ -268,7 +269,7 @@ __global__ void plain_sweep_x_kernel(T *__restrict__ re, T *__restrict__ im, int
 
 // Y sweep: pairs (y, y+1), y = parity + 2q, every column; one thread per
 // (column, pair) with the column fastest so that accesses coalesce.
-template <typename T>
+template <typename T, bool LIFT = false>
 __global__ void plain_sweep_y_kernel(T *__restrict__ re, T *__restrict__ im, int nx, int ny,
                                      int64_t pitch, int parity, T g, T s)
 {
@@ -280,7 +281,7 @@ __global__ void plain_sweep_y_kernel(T *__restrict__ re, T *__restrict__ im, int
         for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx;
              x += gridDim.x * blockDim.x) {
             T ar = r0[x], ai = m0[x], br = r1[x], bi = m1[x];
-            rot2(ar, ai, br, bi, g, s);
+            rot_pair<LIFT>(ar, ai, br, bi, g, s);
             r0[x] = ar;
             m0[x] = ai;
             r1[x] = br;
@@ -403,17 +404,22 @@ cudaError_t launch_phase_table(const double *V, void *pg, void *ps, void *vplane
 }
 
 cudaError_t launch_plain_sweep(void *re, void *im, bool f64, int nx, int ny, int64_t pitch,
-                               int axis, int parity, double g, double s, cudaStream_t st)
+                               int axis, int parity, double g, double s, cudaStream_t st,
+                               bool lift)
 {
     if (axis == 0) {
         dim3 grid = grid2d((nx - parity) / 2, ny);
-        if (f64)
+        if (f64 && lift)
+            plain_sweep_x_kernel<double, true><<<grid, kThreads, 0, st>>>((double *)re, (double *)im, nx, ny, pitch, parity, g, s);
+        else if (f64)
             plain_sweep_x_kernel<double><<<grid, kThreads, 0, st>>>((double *)re, (double *)im, nx, ny, pitch, parity, g, s);
         else
             plain_sweep_x_kernel<float><<<grid, kThreads, 0, st>>>((float *)re, (float *)im, nx, ny, pitch, parity, (float)g, (float)s);
     } else {
         dim3 grid = grid2d(nx, (ny - parity) / 2);
-        if (f64)
+        if (f64 && lift)
+            plain_sweep_y_kernel<double, true><<<grid, kThreads, 0, st>>>((double *)re, (double *)im, nx, ny, pitch, parity, g, s);
+        else if (f64)
             plain_sweep_y_kernel<double><<<grid, kThreads, 0, st>>>((double *)re, (double *)im, nx, ny, pitch, parity, g, s);
         else
             plain_sweep_y_kernel<float><<<grid, kThreads, 0, st>>>((float *)re, (float *)im, nx, ny, pitch, parity, (float)g, (float)s);

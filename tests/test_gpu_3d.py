@@ -49,13 +49,33 @@ def run3(re, im, V, dt, theta, steps, dtype="f32", path="fused"):
 
 
 @pytest.mark.parametrize("nx,ny,nz", [(3, 5, 2), (17, 6, 9), (40, 33, 12)])
-def test_fp64_matches_oracle(nx, ny, nz):
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_fp64_matches_oracle(nx, ny, nz, path):
+    """FP64: ts_evolve merges the sweeps where steps meet (9 n + 3 sweeps in
+    lifting form); ts_evolve_plain runs all 12 per step."""
     rng = np.random.default_rng(nx + 7 * ny + 31 * nz)
     re, im = rand3(rng, nx, ny, nz)
     V = rng.uniform(-0.5, 0.5, (nz, ny, nx))
-    (gre, gim), _ = run3(re, im, V, 0.05, 0.025, 6, dtype="f64")
+    (gre, gim), _ = run3(re, im, V, 0.05, 0.025, 6, dtype="f64", path=path)
     ore, oim = oracle.evolve3(re, im, V, 0.05, 0.025, 6)
     assert rel_l2(gre, gim, ore, oim) < FP64_TOL
+
+
+def test_fp64_launch_count():
+    rng = np.random.default_rng(23)
+    re, im = rand3(rng, 64, 16, 12)
+    g = trotter.Grid(64, 16, "f64", nz=12)
+    try:
+        g.set_state(re, im)
+        g.set_potential(None, 0.05, 0.025)
+        trotter.ts_launch_count(reset=True)
+        g.evolve(5)
+        assert trotter.ts_launch_count() == 10 * 5 + 3     # 9 n + 3 sweeps, n phases
+        trotter.ts_launch_count(reset=True)
+        g.evolve_plain(5)
+        assert trotter.ts_launch_count() == 13 * 5
+    finally:
+        g.close()
 
 
 @pytest.mark.parametrize("nx,ny,nz", [(96, 64, 40), (130, 66, 17), (33, 2, 9), (257, 130, 5),

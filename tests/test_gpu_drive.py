@@ -56,10 +56,11 @@ def run_driven(re, im, V0, V1, a, dt, theta, dtype="f32", path="fused", K=0, chu
 
 
 @pytest.mark.parametrize("nx,ny", [(3, 5), (130, 66), (257, 131)])
-def test_fp64_plain_matches_oracle(nx, ny):
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_fp64_matches_oracle(nx, ny, path):
     rng = np.random.default_rng(nx + 3 * ny)
     re, im, V0, V1, a = drive_inputs(rng, nx, ny, 9)
-    gre, gim = run_driven(re, im, V0, V1, a, 0.05, 0.025, dtype="f64")
+    gre, gim = run_driven(re, im, V0, V1, a, 0.05, 0.025, dtype="f64", path=path)
     ore, oim = oracle.evolve_driven(re, im, V0, V1, a, 0.05, 0.025)
     assert rel_l2(gre, gim, ore, oim) < FP64_TOL
 
@@ -96,6 +97,14 @@ def test_amplitudes_consumed_across_calls():
     gre, gim = run_driven(re, im, V0, V1, a, 0.05, 0.025, K=3, chunks=[5, 1, 11])
     ore, oim = oracle.evolve_driven(re, im, V0, V1, a, 0.05, 0.025)
     assert rel_l2(gre, gim, ore, oim) < FP32_TOL
+
+
+def test_fp64_amplitudes_consumed_across_calls():
+    rng = np.random.default_rng(17)
+    re, im, V0, V1, a = drive_inputs(rng, 70, 45, 12)
+    gre, gim = run_driven(re, im, V0, V1, a, 0.05, 0.025, dtype="f64", chunks=[1, 6, 5])
+    ore, oim = oracle.evolve_driven(re, im, V0, V1, a, 0.05, 0.025)
+    assert rel_l2(gre, gim, ore, oim) < FP64_TOL
 
 
 def test_running_out_of_amplitudes_launches_nothing():

@@ -48,11 +48,14 @@ def run4(re, im, V, dt, theta, steps, dtype="f32", path="fused", K=0):
 
 
 @pytest.mark.parametrize("nx,ny", [(3, 5), (130, 66), (257, 131)])
-def test_fp64_plain_matches_oracle(nx, ny):
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_fp64_matches_oracle(nx, ny, path):
+    """FP64 grids: ts_evolve merges the sweeps where substeps meet (angles
+    2a and a + b there), ts_evolve_plain runs every substep in full."""
     rng = np.random.default_rng(nx * 31 + ny)
     re, im = random_state(rng, nx, ny)
     V = rng.uniform(-0.5, 0.5, (ny, nx))
-    gre, gim = run4(re, im, V, 0.05, 0.025, 7, dtype="f64")
+    gre, gim = run4(re, im, V, 0.05, 0.025, 7, dtype="f64", path=path)
     ore, oim = oracle.evolve(re, im, V, 0.05, 0.025, 7, order=4)
     assert rel_l2(gre, gim, ore, oim) < FP64_TOL
 

@@ -44,13 +44,50 @@ def test_plain_fp64_workload_matches_oracle():
     assert abs(obs["norm"] - 1.0) < 1e-12
 
 
-def test_fp64_grid_default_evolve_is_plain_path():
+def test_fp64_default_evolve_on_the_workload():
+    """ts_evolve on an FP64 grid merges the sweeps where steps meet (one sweep
+    per launch, 6 n + 2 sweeps and n phases for n steps, lifting form):
+    within FP64 rounding of the oracle and of the literal plain sequence."""
     c = wl.plain_fp64_256()
-    (a_re, a_im), _ = run_gpu(c["re"], c["im"], None, c["dt"], c["theta"], 7, dtype="f64",
-                              path="fused", K=0)
-    (b_re, b_im), _ = run_gpu(c["re"], c["im"], None, c["dt"], c["theta"], 7, dtype="f64",
-                              path="plain")
-    assert np.array_equal(a_re, b_re) and np.array_equal(a_im, b_im)
+    (a_re, a_im), _ = run_gpu(c["re"], c["im"], c["V"], c["dt"], c["theta"], c["steps"],
+                              dtype="f64", path="fused", K=0)
+    (b_re, b_im), _ = run_gpu(c["re"], c["im"], c["V"], c["dt"], c["theta"], c["steps"],
+                              dtype="f64", path="plain")
+    ore, oim = oracle.evolve(c["re"], c["im"], c["V"], c["dt"], c["theta"], c["steps"])
+    assert rel_l2(a_re, a_im, ore, oim) < FP64_TOL
+    assert rel_l2(a_re, a_im, b_re, b_im) < FP64_TOL
+
+
+@pytest.mark.parametrize("steps,expected", [(1, 9), (2, 16), (7, 51)])
+def test_fp64_default_evolve_launch_count(steps, expected):
+    rng = np.random.default_rng(3)
+    re, im = random_state(rng, 40, 24)
+    g = trotter.Grid(40, 24, "f64")
+    try:
+        g.set_state(re, im)
+        g.set_potential(None, 0.05, 0.025)
+        trotter.ts_launch_count(reset=True)
+        g.evolve(steps)
+        assert trotter.ts_launch_count() == expected      # 7 n + 2
+        trotter.ts_launch_count(reset=True)
+        g.evolve_plain(steps)
+        assert trotter.ts_launch_count() == 9 * steps
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 2), (3, 5), (17, 33), (1, 64), (64, 1),
+                                   (257, 131), (113, 1000)])
+@pytest.mark.parametrize("dt,theta", [(0.05, 0.025), (-0.05, -0.025), (2.0, 1.3)])
+def test_small_grids_fp64_default(nx, ny, dt, theta):
+    """Merged sweeps at every angle range: theta = 1.3 puts the merged angle
+    2.6 beyond pi/2, where those sweeps take the versine form."""
+    rng = np.random.default_rng(nx * 31 + ny)
+    re, im = random_state(rng, nx, ny)
+    V = rng.uniform(-0.5, 0.5, (ny, nx))
+    (gre, gim), _ = run_gpu(re, im, V, dt, theta, 11, dtype="f64")
+    ore, oim = oracle.evolve(re, im, V, dt, theta, 11)
+    assert rel_l2(gre, gim, ore, oim) < FP64_TOL
 
 
 # ---------------------------------------------------------------------------
