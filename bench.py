@@ -361,15 +361,29 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
         link[name] = round(4.0 * n * n / (a.elapsed_time(b) / 1e3) / 1e9, 1)
     del probe
 
+    # The first grid's uploads go first: the second grid's first uploads wait
+    # for them on the device (otherwise the two share the link and the first
+    # kernels start only after both grids' inputs are in).
+    first_up = [None]
+    first_up_ready = threading.Event()
+
     def e2e_steps(i, count):
         gh, sp_i = grids[i].handle, trotter._VP(streams[i].cuda_stream)
         o_re, o_im = outs[i]
         for k in range(count):
+            if i > 0 and k == 0:
+                if not first_up_ready.wait(120.0):
+                    raise RuntimeError("e2e: the first grid's uploads never started")
+                streams[i].wait_event(first_up[0])
             t = [time.perf_counter()]
             trotter.ts_set_state(gh, hp(h_re), hp(h_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
             t.append(time.perf_counter())
             trotter.ts_set_potential(gh, hp(h_V), trotter.TS_HOST, c["dt"], c["theta"], sp_i)
             t.append(time.perf_counter())
+            if i == 0 and k == 0:
+                first_up[0] = torch.cuda.Event()
+                first_up[0].record(streams[0])
+                first_up_ready.set()
             trotter.ts_evolve(gh, T, K, sp_i)
             t.append(time.perf_counter())
             trotter.ts_get_state(gh, hp(o_re), hp(o_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
@@ -380,16 +394,30 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
                 log.append((i, k, t[0] - t_origin[0]) + tuple(t[m + 1] - t[m] for m in range(5)))
 
     def run_e2e(per_worker):
-        ths = [threading.Thread(target=e2e_steps, args=(i, per_worker)) for i in range(nbuf)]
+        first_up_ready.clear()
+        errors = []
+
+        def worker(i):
+            try:
+                e2e_steps(i, per_worker)
+            except BaseException as exc:      # re-raised below, in the caller
+                errors.append(exc)
+                first_up_ready.set()
+
+        ths = [threading.Thread(target=worker, args=(i,)) for i in range(nbuf)]
         for t in ths:
             t.start()
         for t in ths:
             t.join()
+        if errors:
+            raise errors[0]
 
     run_e2e(max(1, warmup // 2))
     torch.cuda.synchronize()
     dist.barrier()
-    per = max(1, (steps + nbuf - 1) // nbuf)
+    # at least 8 steps: the pipeline's fill (the first uploads) and drain (the
+    # last download) are inside the timed region and are amortised over them
+    per = max(4, (steps + nbuf - 1) // nbuf)
     if log is not None:
         log.clear()
     t0 = t_origin[0] = time.perf_counter()
@@ -402,7 +430,8 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
             "h2d_bytes_per_step": int(n * n * (4 + 4 + 8)),
             "d2h_bytes_per_step": int(n * n * (4 + 4) + 7 * 8),
             "pipeline": "%d grids on %d streams (high and normal priority), one host "
-                        "thread each" % (nbuf, nbuf),
+                        "thread each; the second grid's first uploads wait for the "
+                        "first's" % (nbuf, nbuf),
             "steps": per * nbuf, "link": link}
 
 
