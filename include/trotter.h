@@ -184,9 +184,14 @@ ts_status ts_clear_drive(ts_grid *g);
  * state.  FP32 grids run the fused kernel: K whole steps per HBM round trip
  * on TMA-staged shared-memory tiles (temporal blocking; K = 0 picks the
  * depth automatically, 1 <= K <= 8 forces it; a remainder of steps % K runs
- * at a smaller depth).  FP64 grids run the one-sweep-per-kernel path (K
- * must be 0).  On a grid set to order 4 (ts_set_potential_order) each step
- * is U4(dt): with K = 0 each step is one launch that applies all five
+ * at a smaller depth).  FP64 grids run one sweep per launch (K must be 0,
+ * else TS_ERR_UNSUPPORTED), with the sweeps of one axis merged where two
+ * steps or substeps meet (X, Y and Z factors commute; two factors of one
+ * family add their angles: n second-order steps take 6n + 2 sweeps in 2-D,
+ * 9n + 3 in 3-D) and the lifting form for angles up to pi/2; the results
+ * agree with ts_evolve_plain to FP64 rounding.  On a grid set to order 4
+ * (ts_set_potential_order) each step is U4(dt): on FP32 grids with K = 0
+ * each step is one launch that applies all five
  * substeps; with K >= 1 the p dt substeps of neighbouring steps run as
  * fused launches of depth at most K and each (1-4p) dt substep as a
  * depth-1 launch.  Async. */
