@@ -220,7 +220,11 @@ ts_status ts_expect_xy(ts_grid *g, double *x, double *y, void *stream);
 ts_status ts_energy(ts_grid *g, double *out, void *stream);   /* e_kin + e_pot */
 
 /* Evolve n independent grids (steps[i] steps each, fused depth K as in
- * ts_evolve) on one stream.  Async. */
+ * ts_evolve) on one stream.  Second-order 2-D FP32 grids with |theta| <=
+ * pi/4 and no drive advance together in multi-grid launches of the fused
+ * kernel; every other grid runs ts_evolve on its own (FP64 grids with K = 0,
+ * whatever K is given).  Errors: TS_ERR_ARG (n < 0, NULL arrays, a NULL grid
+ * or negative steps), then those of ts_evolve.  Async. */
 ts_status ts_evolve_batched(ts_grid *const *g, int n, const int64_t *steps, int K,
                             void *stream);
 

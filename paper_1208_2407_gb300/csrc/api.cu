@@ -980,7 +980,8 @@ ts_status ts_evolve_batched(ts_grid *const *gs, int n, const int64_t *steps, int
         if (steps[i] == 0) continue;
         if (gs[i]->f64() || gs[i]->order != 2 || gs[i]->driven || gs[i]->is3d() ||
             std::fabs(gs[i]->theta) > 0.25 * M_PI) {
-            ts_status s = ts_evolve(gs[i], steps[i], K, stream);
+            // K is the fused FP32 depth; FP64 grids take their own sequence
+            ts_status s = ts_evolve(gs[i], steps[i], gs[i]->f64() ? 0 : K, stream);
             if (s != TS_OK) return s;
         } else {
             multi.push_back(gs[i]);

@@ -265,26 +265,29 @@ def test_state_round_trip_host_and_device(dtype):
 
 
 def test_batched_equals_individual():
+    """FP32 grids share one multi-grid launch sequence; an FP64 grid in the
+    batch runs its own sequence (K applies to FP32 grids only)."""
     rng = np.random.default_rng(8)
-    shapes = [(64, 40), (130, 66), (33, 257)]
-    steps = [5, 9, 12]
+    shapes = [(64, 40, "f32"), (130, 66, "f32"), (33, 257, "f32"), (50, 30, "f64")]
+    steps = [5, 9, 12, 7]
     grids, inputs = [], []
-    for (nx, ny) in shapes:
+    for (nx, ny, dtype) in shapes:
         re, im = random_state(rng, nx, ny)
         V = rng.uniform(-0.5, 0.5, (ny, nx))
-        g = trotter.Grid(nx, ny, "f32")
+        g = trotter.Grid(nx, ny, dtype)
         g.set_state(re, im)
         g.set_potential(V, 0.05, 0.025)
         grids.append(g)
-        inputs.append((re, im, V))
+        inputs.append((re, im, V, dtype))
     try:
         trotter.evolve_batched(grids, steps, K=3)
         outs = [g.get_state(np.float64) for g in grids]
     finally:
         for g in grids:
             g.close()
-    for (re, im, V), s, (gre, gim) in zip(inputs, steps, outs):
-        (b_re, b_im), _ = run_gpu(re, im, V, 0.05, 0.025, s, K=3)
+    for (re, im, V, dtype), s, (gre, gim) in zip(inputs, steps, outs):
+        K = 3 if dtype == "f32" else 0
+        (b_re, b_im), _ = run_gpu(re, im, V, 0.05, 0.025, s, dtype=dtype, K=K)
         assert np.array_equal(gre, b_re) and np.array_equal(gim, b_im)
 
 
