@@ -128,9 +128,12 @@ ts_status ts_get_state(ts_grid *g, void *re, void *im, ts_dtype dst_dtype,
  * host or device memory, or NULL for V = 0.  dt: the time step; theta: the
  * kinetic half-step angle J*dt/2 (hopping J = 2 theta / dt).  On the device
  * the per-site table (gamma_V = 1 - cos(V dt), s_V = sin(V dt)) is computed
- * in FP64 and rounded once to the grid's dtype; the kinetic rotation is
- * applied in the same versine form (1 - cos theta, sin theta), computed in
- * FP64 and rounded once.  Async (host V: returns when V may be reused). */
+ * to FP64 accuracy (FP64 for FP64 grids; double-float arithmetic for FP32
+ * grids, within one ulp of the FP64 value rounded) and rounded once to the
+ * grid's dtype.  The kinetic coefficients (1 - cos theta, sin theta,
+ * tan(theta/2), and those of 2 theta for merged sweeps) are computed in
+ * FP64 on the host and rounded once.  Async (host V: returns when V may be
+ * reused). */
 ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
                            double theta, void *stream);
 
