@@ -239,7 +239,7 @@ def run_reference(args):
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in ("fused.cu", "common.cuh", "ffloat.cuh", "internal.h"):
+    for name in ("fused.cu", "common.cuh", "ffloat.cuh", "internal.h", "mbar.cuh"):
         with open(os.path.join(ROOT, "paper_1208_2407_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -205,6 +205,19 @@ ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream);
  * fused path is measured against.  Async. */
 ts_status ts_evolve_plain(ts_grid *g, int64_t steps, void *stream);
 
+/* Check of the failure path of the bounded device waits.  Every mbarrier
+ * wait in the fused kernels gives up after a time limit (2 s), sets a bit in
+ * the grid's error word and returns, so a TMA copy that never lands is
+ * reported instead of hanging the GPU.  This call enqueues one warp that runs
+ * the same bounded wait on an mbarrier nothing completes (no copy in
+ * flight), for limit_ns nanoseconds, and sets the same bit in g's error
+ * word.  The grid's state and tables are not touched.  The next syncing
+ * call on g (ts_get_state, ts_observe, ts_norm, ...) then returns
+ * TS_ERR_TIMEOUT and clears the word; later calls work as before.
+ * Errors: TS_ERR_ARG (NULL grid, limit_ns outside [1e3, 2e9]), TS_ERR_CUDA.
+ * Async. */
+ts_status ts_check_wait_timeout(ts_grid *g, int64_t limit_ns, void *stream);
+
 /* Observables of the current state, reduced on the device with FP64
  * compensated (Neumaier) partial sums, finished on the device, copied back.
  * Syncs `stream`. */

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtrotter.so")
 SOURCES = ["api.cu", "plain.cu", "fused.cu", "reduce.cu", "adjoint.cu", "server.cu",
-           "noalloc.cu", "lattice3d.cu"]
+           "noalloc.cu", "lattice3d.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

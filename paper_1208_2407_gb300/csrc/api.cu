@@ -955,6 +955,17 @@ ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
     return fused_steps(g, steps, K == 0 ? auto_depth() : K, st);
 }
 
+ts_status ts_check_wait_timeout(ts_grid *g, int64_t limit_ns, void *stream)
+{
+    if (!g) return fail(TS_ERR_ARG, "ts_check_wait_timeout: grid is NULL");
+    if (limit_ns < 1000 || limit_ns > 2000000000)
+        return fail(TS_ERR_ARG, "ts_check_wait_timeout: limit_ns must be in [1e3, 2e9], got %lld",
+                    (long long)limit_ns);
+    cudaError_t e = ts::launch_wait_timeout_check(g->err, (uint64_t)limit_ns, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wait-timeout check launch");
+    return TS_OK;
+}
+
 ts_status ts_evolve_plain(ts_grid *g, int64_t steps, void *stream)
 {
     if (!g) return fail(TS_ERR_ARG, "ts_evolve_plain: grid is NULL");

@@ -42,6 +42,12 @@ cudaError_t launch_plain_phase(void *re, void *im, const void *pg, const void *p
 cudaError_t launch_plain_drive(void *re, void *im, const void *v1, bool f64, int nx, int ny,
                                int64_t pitch, double adt, cudaStream_t st);
 
+// --- failure path of the bounded waits (selftest.cu) ----------------------
+// One warp waits on an mbarrier that nothing completes; after limit_ns the
+// wait gives up and ERRBIT_WAIT_TIMEOUT is or-ed into *err, as in the fused
+// kernels.
+cudaError_t launch_wait_timeout_check(int *err, uint64_t limit_ns, cudaStream_t st);
+
 // --- three-dimensional lattices (lattice3d.cu) ----------------------------
 // A 3-D grid of nx x ny x nz sites keeps slab z (rows z*ny .. z*ny + ny - 1
 // of every plane) right after slab z - 1, so the 2-D kernels see a grid of

@@ -94,6 +94,7 @@ _SIGNATURES = {
     "ts_clear_drive": [_VP],
     "ts_evolve": [_VP, _I64, _INT, _VP],
     "ts_evolve_plain": [_VP, _I64, _VP],
+    "ts_check_wait_timeout": [_VP, _I64, _VP],
     "ts_observe": [_VP, ctypes.POINTER(ts_observables), _VP],
     "ts_norm": [_VP, ctypes.POINTER(_DBL), _VP],
     "ts_expect_xy": [_VP, ctypes.POINTER(_DBL), ctypes.POINTER(_DBL), _VP],
@@ -222,6 +223,10 @@ def ts_clear_drive(h):
 
 def ts_evolve_plain(h, steps, stream):
     _call("ts_evolve_plain", h, steps, stream)
+
+
+def ts_check_wait_timeout(h, limit_ns, stream):
+    _call("ts_check_wait_timeout", h, limit_ns, stream)
 
 
 def ts_observe(h, stream) -> ts_observables:
