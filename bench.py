@@ -324,7 +324,7 @@ def serve_bench(n_requests: int, seed: int, budget_gb: float = 120.0):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
+def e2e_bench(c, n, T, K, steps, warmup, dist, log=None, nbuf=2):
     """End to end through the C ABI with pinned host buffers.  Each step
     uploads psi (FP32) and V (FP64) from pinned host memory, runs the step and
     reads the state and the observables back.  Two grids on two streams,
@@ -334,7 +334,6 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
     start, set_state, set_potential, evolve, get_state, observe) times."""
     import torch
     from paper_1208_2407_gb300 import trotter
-    nbuf = 2
     grids = [trotter.Grid(n, n, "f32") for _ in range(nbuf)]
     # unequal priorities keep the two grids out of step: the first grid's
     # kernels go first, and the second grid's copies overlap them (equal
@@ -361,29 +360,29 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
         link[name] = round(4.0 * n * n / (a.elapsed_time(b) / 1e3) / 1e9, 1)
     del probe
 
-    # The first grid's uploads go first: the second grid's first uploads wait
-    # for them on the device (otherwise the two share the link and the first
-    # kernels start only after both grids' inputs are in).
-    first_up = [None]
-    first_up_ready = threading.Event()
+    # The grids' first uploads go one after another: grid i's wait for grid
+    # i - 1's on the device (otherwise they share the link and the first
+    # kernels start only after every grid's inputs are in).
+    first_up = [None] * nbuf
+    first_up_ready = [threading.Event() for _ in range(nbuf)]
 
     def e2e_steps(i, count):
         gh, sp_i = grids[i].handle, trotter._VP(streams[i].cuda_stream)
         o_re, o_im = outs[i]
         for k in range(count):
             if i > 0 and k == 0:
-                if not first_up_ready.wait(120.0):
-                    raise RuntimeError("e2e: the first grid's uploads never started")
-                streams[i].wait_event(first_up[0])
+                if not first_up_ready[i - 1].wait(120.0):
+                    raise RuntimeError("e2e: grid %d's first uploads never started" % (i - 1))
+                streams[i].wait_event(first_up[i - 1])
             t = [time.perf_counter()]
             trotter.ts_set_state(gh, hp(h_re), hp(h_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
             t.append(time.perf_counter())
             trotter.ts_set_potential(gh, hp(h_V), trotter.TS_HOST, c["dt"], c["theta"], sp_i)
             t.append(time.perf_counter())
-            if i == 0 and k == 0:
-                first_up[0] = torch.cuda.Event()
-                first_up[0].record(streams[0])
-                first_up_ready.set()
+            if k == 0:
+                first_up[i] = torch.cuda.Event()
+                first_up[i].record(streams[i])
+                first_up_ready[i].set()
             trotter.ts_evolve(gh, T, K, sp_i)
             t.append(time.perf_counter())
             trotter.ts_get_state(gh, hp(o_re), hp(o_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
@@ -394,7 +393,8 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
                 log.append((i, k, t[0] - t_origin[0]) + tuple(t[m + 1] - t[m] for m in range(5)))
 
     def run_e2e(per_worker):
-        first_up_ready.clear()
+        for ev in first_up_ready:
+            ev.clear()
         errors = []
 
         def worker(i):
@@ -402,7 +402,8 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
                 e2e_steps(i, per_worker)
             except BaseException as exc:      # re-raised below, in the caller
                 errors.append(exc)
-                first_up_ready.set()
+                for ev in first_up_ready:
+                    ev.set()
 
         ths = [threading.Thread(target=worker, args=(i,)) for i in range(nbuf)]
         for t in ths:
@@ -417,7 +418,7 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
     dist.barrier()
     # at least 8 steps: the pipeline's fill (the first uploads) and drain (the
     # last download) are inside the timed region and are amortised over them
-    per = max(4, (steps + nbuf - 1) // nbuf)
+    per = max((8 + nbuf - 1) // nbuf, (steps + nbuf - 1) // nbuf)
     if log is not None:
         log.clear()
     t0 = t_origin[0] = time.perf_counter()
@@ -430,8 +431,8 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None):
             "h2d_bytes_per_step": int(n * n * (4 + 4 + 8)),
             "d2h_bytes_per_step": int(n * n * (4 + 4) + 7 * 8),
             "pipeline": "%d grids on %d streams (high and normal priority), one host "
-                        "thread each; the second grid's first uploads wait for the "
-                        "first's" % (nbuf, nbuf),
+                        "thread each; each grid's first uploads wait for the previous "
+                        "grid's" % (nbuf, nbuf),
             "steps": per * nbuf, "link": link}
 
 
