@@ -168,17 +168,22 @@ cudaError_t evolve_multi(ts_grid *const *gs, const int64_t *steps, int n, int K,
     cudaError_t e = cudaMallocAsync((void **)&tab, sizeof(EpochEntry) * (size_t)n, st);
     if (e != cudaSuccess) return e;
     std::vector<EpochEntry> h;
+    std::vector<int> hx, hy;
     auto run = [&](int depth, const std::vector<int> &idx, int64_t launches) -> cudaError_t {
         h.clear();
-        int64_t units = 0;
+        hx.clear();
+        hy.clear();
         for (int i : idx) {
-            h.push_back(EpochEntry{gs[i]->desc_dev, units, gs[i]->cur, 0});
-            units += fused_units(depth, (int)gs[i]->L.nx, (int)gs[i]->L.ny);
+            h.push_back(EpochEntry{gs[i]->desc_dev, 0, gs[i]->cur, 0});
+            hx.push_back((int)gs[i]->L.nx);
+            hy.push_back((int)gs[i]->L.ny);
         }
+        const MultiPlan plan = fused_multi_plan(depth, (int)h.size(), hx.data(), hy.data(), h.data());
+        if (plan.warps < 1) return cudaErrorInvalidConfiguration;
         cudaError_t err = cudaMemcpyAsync(tab, h.data(), sizeof(EpochEntry) * h.size(),
                                           cudaMemcpyHostToDevice, st);
         for (int64_t t = 0; t < launches && err == cudaSuccess; ++t)
-            err = launch_fused_multi(depth, tab, (int)h.size(), units, (int)(t & 1),
+            err = launch_fused_multi(depth, tab, (int)h.size(), plan, (int)(t & 1),
                                      gs[idx[0]]->err, st);
         if (err == cudaSuccess && (launches & 1))
             for (int i : idx) gs[i]->cur ^= 1;

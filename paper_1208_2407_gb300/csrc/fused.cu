@@ -41,7 +41,11 @@
 // Every wait on an mbarrier is bounded (globaltimer): on a timeout the warp
 // sets an error bit, waits (bounded) for its own outstanding copies and
 // returns; the host reports TS_ERR_TIMEOUT at its next synchronising call.
+#include <algorithm>
 #include <cstdio>
+#include <queue>
+#include <utility>
+#include <vector>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
@@ -884,14 +888,39 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
     }
 }
 
-// Many grids in one persistent launch (the serving path): the units of all
-// the grids of an epoch table, concatenated in table order, are split into
-// equal contiguous ranges, one per warp.  A grid's tensor maps live in its
-// descriptor in global memory, written once when the grid was set up.
+// Many grids in one persistent launch (the serving path), under one of two
+// plans (fused_multi_plan picks one per launch):
+//  - aligned: grid i owns warps [begin, begin + strips * strip_warps),
+//    strip_warps per strip on the same row ranges in every strip (as in the
+//    single-grid kernel's aligned split), so warps of neighbouring strips
+//    walk the same rows together and read their shared halo columns from L2;
+//  - even: the row pairs of all grids, concatenated in table order (grid i's
+//    from unit `begin` on), are split into equal contiguous ranges, one per
+//    warp -- balanced for any mix, but without that alignment.
+// A grid's tensor maps live in its descriptor in global memory, written once
+// when the grid was set up.
+__device__ __forceinline__ void multi_params(KParams &p, const GridDesc *d, int cur, int *err)
+{
+    p.nx = d->nx;
+    p.ny = d->ny;
+    p.pitch = d->pitch;
+    p.out_re = d->re[cur ^ 1];
+    p.out_im = d->im[cur ^ 1];
+    p.t1 = d->t1;
+    p.s1 = d->s1;
+    p.g1 = d->g1;
+    p.t2 = d->t2;
+    p.s2 = d->s2;
+    p.err = err;
+    p.n_pairs = (p.ny + 1) / 2;
+    p.strip_warps = 0;
+    p.ny_slab = 0;
+}
+
 template <int K>
 __global__ void __launch_bounds__(Cfg<K>::WPC * 32, multi_min_blocks(K))
 fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t total_units,
-                   int total_warps, int flip, int *err)
+                   int total_warps, int aligned, int flip, int *err)
 {
     using C = Cfg<K>;
     extern __shared__ unsigned char smem_raw[];
@@ -899,11 +928,39 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
     const int gw = blockIdx.x * C::WPC + warp;
     if (gw >= total_warps) return;
     WarpRings r = carve_rings<K>(smem_raw, warp, lane);
+    if (aligned) {
+        // the grid of warp gw: the last entry whose first warp is <= gw
+        int lo = 0, hi = n_grids - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab[mid].begin <= gw)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const EpochEntry e = tab[lo];
+        const GridDesc *d = e.desc;
+        const int cur = e.cur0 ^ flip;
+        if (lane == 0) {
+            tensormap_acquire(&d->tm_state[cur]);
+            tensormap_acquire(&d->tm_phase);
+        }
+        __syncwarp();
+        KParams p;
+        multi_params(p, d, cur, err);
+        const int w = e.strip_warps, l = gw - (int)e.begin;
+        const int sx = l / w, i = l - sx * w;
+        const int q0 = (int)((int64_t)i * p.n_pairs / w);
+        const int q1 = (int)((int64_t)(i + 1) * p.n_pairs / w);
+        if (q1 > q0)
+            run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, p, sx, q0, q1, lane);
+        return;
+    }
     const int64_t u_begin = (int64_t)gw * total_units / total_warps;
     const int64_t u_end = (int64_t)(gw + 1) * total_units / total_warps;
     int gi = 0, fenced = -1;
     for (int64_t u = u_begin; u < u_end;) {
-        while (gi + 1 < n_grids && tab[gi + 1].unit_begin <= u) ++gi;
+        while (gi + 1 < n_grids && tab[gi + 1].begin <= u) ++gi;
         const EpochEntry e = tab[gi];
         const GridDesc *d = e.desc;
         const int cur = e.cur0 ^ flip;
@@ -916,23 +973,9 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
             fenced = gi;
         }
         KParams p;
-        p.nx = d->nx;
-        p.ny = d->ny;
-        p.pitch = d->pitch;
-        p.out_re = d->re[cur ^ 1];
-        p.out_im = d->im[cur ^ 1];
-        p.t1 = d->t1;
-        p.s1 = d->s1;
-        p.g1 = d->g1;
-        p.t2 = d->t2;
-        p.s2 = d->s2;
-        p.err = err;
-        p.n_pairs = (p.ny + 1) / 2;
-        p.strip_warps = 0;
-        p.ny_slab = 0;
-        const int64_t local = u - e.unit_begin;
-        const int64_t g_units = (gi + 1 < n_grids ? tab[gi + 1].unit_begin : total_units) -
-                                e.unit_begin;
+        multi_params(p, d, cur, err);
+        const int64_t local = u - e.begin;
+        const int64_t g_units = (gi + 1 < n_grids ? tab[gi + 1].begin : total_units) - e.begin;
         const int sx = (int)(local / p.n_pairs);
         const int q0 = (int)(local - (int64_t)sx * p.n_pairs);
         int64_t q1_want = (int64_t)q0 + (u_end - u);
@@ -1038,13 +1081,6 @@ cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st)
     }
 }
 
-int64_t fused_units(int K, int nx, int ny)
-{
-    const int halo = ((2 * K + 3) / 4) * 4;
-    const int valid = FUSED_BOX_COLS - 2 * halo;
-    return (int64_t)((nx + valid - 1) / valid) * ((ny + 1) / 2);
-}
-
 template <int K>
 const Occupancy &multi_occupancy()
 {
@@ -1060,21 +1096,25 @@ cudaError_t prepare_multi_k()
 }
 
 template <int K>
-cudaError_t launch_multi_k(const EpochEntry *tab, int n_grids, int64_t total_units, int flip,
+cudaError_t launch_multi_k(const EpochEntry *tab, int n_grids, const MultiPlan &plan, int flip,
                            int *err, cudaStream_t st)
 {
     using C = Cfg<K>;
     const Occupancy &occ = multi_occupancy<K>();
     if (occ.err != cudaSuccess) return occ.err;
-    const int blocks_per_sm = occ.blocks_per_sm, num_sms = occ.num_sms;
-    int64_t want = (total_units + 15) / 16;
-    int64_t cap = (int64_t)num_sms * blocks_per_sm * C::WPC;
-    const int total_warps = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-    const int blocks = (total_warps + C::WPC - 1) / C::WPC;
-    fused_multi_kernel<K><<<blocks, C::WPC * 32, C::SMEM, st>>>(tab, n_grids, total_units,
-                                                               total_warps, flip, err);
+    const int blocks = (plan.warps + C::WPC - 1) / C::WPC;
+    fused_multi_kernel<K><<<blocks, C::WPC * 32, C::SMEM, st>>>(
+        tab, n_grids, plan.units, plan.warps, plan.aligned ? 1 : 0, flip, err);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <int K>
+int64_t multi_capacity()
+{
+    const Occupancy &occ = multi_occupancy<K>();
+    if (occ.err != cudaSuccess) return -1;
+    return (int64_t)occ.num_sms * occ.blocks_per_sm * Cfg<K>::WPC;
 }
 
 cudaError_t fused_multi_prepare(int K)
@@ -1092,21 +1132,81 @@ cudaError_t fused_multi_prepare(int K)
     }
 }
 
-cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, int64_t total_units,
+cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, const MultiPlan &plan,
                                int flip, int *err, cudaStream_t st)
 {
-    if (n_grids < 1 || total_units < 1) return cudaSuccess;
+    if (n_grids < 1 || plan.warps < 1 || plan.units < 1) return cudaSuccess;
     switch (K) {
-    case 1: return launch_multi_k<1>(tab, n_grids, total_units, flip, err, st);
-    case 2: return launch_multi_k<2>(tab, n_grids, total_units, flip, err, st);
-    case 3: return launch_multi_k<3>(tab, n_grids, total_units, flip, err, st);
-    case 4: return launch_multi_k<4>(tab, n_grids, total_units, flip, err, st);
-    case 5: return launch_multi_k<5>(tab, n_grids, total_units, flip, err, st);
-    case 6: return launch_multi_k<6>(tab, n_grids, total_units, flip, err, st);
-    case 7: return launch_multi_k<7>(tab, n_grids, total_units, flip, err, st);
-    case 8: return launch_multi_k<8>(tab, n_grids, total_units, flip, err, st);
+    case 1: return launch_multi_k<1>(tab, n_grids, plan, flip, err, st);
+    case 2: return launch_multi_k<2>(tab, n_grids, plan, flip, err, st);
+    case 3: return launch_multi_k<3>(tab, n_grids, plan, flip, err, st);
+    case 4: return launch_multi_k<4>(tab, n_grids, plan, flip, err, st);
+    case 5: return launch_multi_k<5>(tab, n_grids, plan, flip, err, st);
+    case 6: return launch_multi_k<6>(tab, n_grids, plan, flip, err, st);
+    case 7: return launch_multi_k<7>(tab, n_grids, plan, flip, err, st);
+    case 8: return launch_multi_k<8>(tab, n_grids, plan, flip, err, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+MultiPlan fused_multi_plan(int K, int n, const int *nx, const int *ny, EpochEntry *tab)
+{
+    MultiPlan plan = {0, 0, false};
+    int64_t cap;
+    switch (K) {
+    case 1: cap = multi_capacity<1>(); break;
+    case 2: cap = multi_capacity<2>(); break;
+    case 3: cap = multi_capacity<3>(); break;
+    case 4: cap = multi_capacity<4>(); break;
+    case 5: cap = multi_capacity<5>(); break;
+    case 6: cap = multi_capacity<6>(); break;
+    case 7: cap = multi_capacity<7>(); break;
+    case 8: cap = multi_capacity<8>(); break;
+    default: return plan;
+    }
+    if (cap < 1 || n < 1) return plan;
+    const int halo = ((2 * K + 3) / 4) * 4, valid = FUSED_BOX_COLS - 2 * halo;
+    std::vector<int64_t> strips((size_t)n), pairs((size_t)n), w((size_t)n, 1);
+    int64_t units = 0, all_strips = 0;
+    for (int i = 0; i < n; ++i) {
+        strips[(size_t)i] = (nx[i] + valid - 1) / valid;
+        pairs[(size_t)i] = (ny[i] + 1) / 2;
+        units += strips[(size_t)i] * pairs[(size_t)i];
+        all_strips += strips[(size_t)i];
+    }
+    // even split: at least ~16 row pairs per warp, at most the resident warps
+    const int64_t lin_warps = std::min(cap, std::max<int64_t>(1, (units + 15) / 16));
+    const int64_t lin_span = (units + lin_warps - 1) / lin_warps;
+    // aligned split: one warp per strip to start with, then more warps (on
+    // every strip of a grid at once) to the grid with the most row pairs per
+    // warp while they fit; it is taken when its longest warp is within 10 %
+    // of the even split's
+    int64_t al_warps = all_strips, al_span = 0;
+    if (all_strips <= cap) {
+        auto work = [&](int i) { return (pairs[(size_t)i] + w[(size_t)i] - 1) / w[(size_t)i]; };
+        std::priority_queue<std::pair<int64_t, int>> heap;
+        for (int i = 0; i < n; ++i) heap.push({work(i), i});
+        while (!heap.empty()) {
+            const int i = heap.top().second;
+            if (al_warps + strips[(size_t)i] > cap || pairs[(size_t)i] / (w[(size_t)i] + 1) < 16)
+                break;
+            heap.pop();
+            ++w[(size_t)i];
+            al_warps += strips[(size_t)i];
+            heap.push({work(i), i});
+        }
+        for (int i = 0; i < n; ++i) al_span = std::max(al_span, work(i));
+    }
+    plan.aligned = all_strips <= cap && al_span * 10 <= lin_span * 11;
+    plan.units = units;
+    int64_t begin = 0;
+    for (int i = 0; i < n; ++i) {
+        tab[i].begin = begin;
+        tab[i].strip_warps = plan.aligned ? (int)w[(size_t)i] : 0;
+        begin += plan.aligned ? strips[(size_t)i] * w[(size_t)i] : strips[(size_t)i] * pairs[(size_t)i];
+    }
+    plan.warps = (int)(plan.aligned ? al_warps : lin_warps);
+    return plan;
 }
 
 cudaError_t launch_fused_drive(int K, const FusedLaunch &a, cudaStream_t st)

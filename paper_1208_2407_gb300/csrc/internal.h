@@ -147,22 +147,36 @@ struct GridDesc {
     float t1, s1, g1, t2, s2;  // rotation coefficients (see FusedLaunch)
 };
 
-// One grid of an epoch: its descriptor, the first of its units in the
-// concatenated unit list, and which pair holds its state at flip = 0.
+// One grid of an epoch: its descriptor, where its work starts in the
+// launch's plan (its first warp in an aligned plan, its first row-pair unit
+// in an even one), its warps per strip (aligned plans), and which pair holds
+// its state at flip = 0.
 struct EpochEntry {
     const GridDesc *desc;
-    int64_t unit_begin;
+    int64_t begin;
     int cur0;
-    int pad;
+    int strip_warps;
+};
+
+// How one multi-grid launch splits its work over warps.
+struct MultiPlan {
+    int warps;       // warps launched
+    int64_t units;   // row-pair units of all grids (strips x row pairs)
+    bool aligned;    // strip-aligned (per-grid warps per strip) or even split
 };
 
 // Set the multi-grid kernel's attributes for depth K (call outside stream capture).
 cudaError_t fused_multi_prepare(int K);
-// Units (strip x row-pair work items) of an nx x ny grid at depth K.
-int64_t fused_units(int K, int nx, int ny);
-// K steps for every grid of a device epoch table; the input pair of grid i
-// is tab[i].cur0 ^ flip.
-cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, int64_t total_units,
+// Plan one multi-grid launch at depth K over n grids (sides nx[i] x ny[i])
+// and fill tab[i].begin and tab[i].strip_warps (the caller sets desc and
+// cur0).  The strip-aligned split (every strip of a grid on the same row
+// ranges, so neighbouring strips share halo columns through L2) is taken
+// when its longest warp is within 10 % of the even split's; mixes of many
+// small grids get the even split.  warps == 0 on an error.
+MultiPlan fused_multi_plan(int K, int n, const int *nx, const int *ny, EpochEntry *tab);
+// K steps for every grid of a device epoch table planned by
+// fused_multi_plan; the input pair of grid i is tab[i].cur0 ^ flip.
+cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, const MultiPlan &plan,
                                int flip, int *err, cudaStream_t st);
 
 // Build a 3-D FP32 tensor map over `planes` (2 to 4) consecutive pitched

@@ -85,10 +85,13 @@ struct Epoch {
 
 struct GraphKey {
     int slot, n, L, K;
+    int warps;
     int64_t units;
+    bool aligned;
     bool operator==(const GraphKey &o) const
     {
-        return slot == o.slot && n == o.n && L == o.L && K == o.K && units == o.units;
+        return slot == o.slot && n == o.n && L == o.L && K == o.K && warps == o.warps &&
+               units == o.units && aligned == o.aligned;
     }
 };
 
@@ -127,7 +130,7 @@ struct ts_server {
     void enqueue_epoch(std::unique_lock<std::mutex> &lk);
     void retire(Epoch &e, bool ok);
     int take_table();
-    cudaError_t launch_full(int slot, int n, int64_t units, int L);
+    cudaError_t launch_full(int slot, int n, const ts::MultiPlan &plan, int L);
 };
 
 int ts_server::take_table()
@@ -138,11 +141,11 @@ int ts_server::take_table()
     return s;
 }
 
-cudaError_t ts_server::launch_full(int slot, int n, int64_t units, int L)
+cudaError_t ts_server::launch_full(int slot, int n, const ts::MultiPlan &plan, int L)
 {
     const ts::EpochEntry *tab = tab_dev + (size_t)slot * cfg.max_slots;
-    if (L == 1) return ts::launch_fused_multi(K, tab, n, units, 0, err_dev, compute);
-    const GraphKey key{slot, n, L, K, units};
+    if (L == 1) return ts::launch_fused_multi(K, tab, n, plan, 0, err_dev, compute);
+    const GraphKey key{slot, n, L, K, plan.warps, plan.units, plan.aligned};
     for (auto &kv : graphs)
         if (kv.first == key) {
             ++graph_launches;
@@ -152,7 +155,7 @@ cudaError_t ts_server::launch_full(int slot, int n, int64_t units, int L)
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(compute, cudaStreamCaptureModeThreadLocal);
     for (int t = 0; t < L && e == cudaSuccess; ++t)
-        e = ts::launch_fused_multi(K, tab, n, units, t & 1, err_dev, compute);
+        e = ts::launch_fused_multi(K, tab, n, plan, t & 1, err_dev, compute);
     cudaError_t e2 = cudaStreamEndCapture(compute, &graph);
     if (e == cudaSuccess) e = e2;
     cudaGraphExec_t exec = nullptr;
@@ -295,14 +298,17 @@ void ts_server::enqueue_epoch(std::unique_lock<std::mutex> &lk)
     for (auto &q : run_full) L = std::min(L, q->full_left);
     lk.unlock();
     cudaError_t e = cudaSuccess;
-    auto upload = [&](const std::vector<ReqP> &set, int depth, int64_t &units) -> int {
+    auto upload = [&](const std::vector<ReqP> &set, int depth, ts::MultiPlan &plan) -> int {
         const int slot = take_table();
         ts::EpochEntry *h = tab_host + (size_t)slot * cfg.max_slots;
-        units = 0;
+        std::vector<int> nx(set.size()), ny(set.size());
         for (size_t i = 0; i < set.size(); ++i) {
-            h[i] = ts::EpochEntry{set[i]->g->desc_dev, units, set[i]->g->cur, 0};
-            units += ts::fused_units(depth, (int)set[i]->r.nx, (int)set[i]->r.ny);
+            h[i] = ts::EpochEntry{set[i]->g->desc_dev, 0, set[i]->g->cur, 0};
+            nx[i] = (int)set[i]->r.nx;
+            ny[i] = (int)set[i]->r.ny;
         }
+        plan = ts::fused_multi_plan(depth, (int)set.size(), nx.data(), ny.data(), h);
+        if (plan.warps < 1 && e == cudaSuccess) e = cudaErrorInvalidConfiguration;
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(tab_dev + (size_t)slot * cfg.max_slots, h,
                                 sizeof(ts::EpochEntry) * set.size(), cudaMemcpyHostToDevice, compute);
@@ -310,11 +316,11 @@ void ts_server::enqueue_epoch(std::unique_lock<std::mutex> &lk)
         return slot;
     };
     if (!run_full.empty()) {
-        int64_t units = 0;
-        const int slot = upload(run_full, K, units);
+        ts::MultiPlan plan{};
+        const int slot = upload(run_full, K, plan);
         if (e != cudaSuccess) where = "epoch table upload";
         if (e == cudaSuccess) {
-            e = launch_full(slot, (int)run_full.size(), units, (int)L);
+            e = launch_full(slot, (int)run_full.size(), plan, (int)L);
             if (e != cudaSuccess) where = L > 1 ? "epoch graph" : "epoch launch";
         }
     }
@@ -323,11 +329,11 @@ void ts_server::enqueue_epoch(std::unique_lock<std::mutex> &lk)
     for (auto &q : run_rem) by_rem[q->rem_left].push_back(q);
     for (int r = 1; r < K && e == cudaSuccess; ++r) {
         if (by_rem[r].empty()) continue;
-        int64_t units = 0;
-        const int slot = upload(by_rem[r], r, units);
+        ts::MultiPlan plan{};
+        const int slot = upload(by_rem[r], r, plan);
         if (e == cudaSuccess) {
             e = ts::launch_fused_multi(r, tab_dev + (size_t)slot * cfg.max_slots,
-                                       (int)by_rem[r].size(), units, 0, err_dev, compute);
+                                       (int)by_rem[r].size(), plan, 0, err_dev, compute);
             if (e != cudaSuccess) where = "remainder launch";
         }
     }
