@@ -87,6 +87,15 @@ namespace {
 #ifndef TS_FUSED_MULTI_MIN_BLOCKS_K4   // multi-grid kernel, K = 4
 #define TS_FUSED_MULTI_MIN_BLOCKS_K4 1
 #endif
+#ifndef TS_FUSED_MIN_PAIRS       // row pairs per warp: at least this many ...
+#define TS_FUSED_MIN_PAIRS 4
+#endif
+#ifndef TS_FUSED_MAX_MIN_PAIRS   // ... and at most this many as the floor
+#define TS_FUSED_MAX_MIN_PAIRS 16
+#endif
+#ifndef TS_FUSED_FILL_WARPS_PER_SM   // warps per SM that keep HBM busy
+#define TS_FUSED_FILL_WARPS_PER_SM 8
+#endif
 #ifndef TS_FUSED_PINGPONG_MIN_K  // interior row pairs alternate two carry sets for K in
 #define TS_FUSED_PINGPONG_MIN_K 3    // [MIN_K, MAX_K] (beyond MAX_K the second set spills)
 #endif
@@ -995,6 +1004,19 @@ struct Occupancy {
     int blocks_per_sm, num_sms;
 };
 
+// Fewest row pairs a warp takes.  Each warp runs a chain of dependent
+// iterations, and each of its segments first fills a pipeline of 2K row
+// pairs.  On small grids the chains set the launch time, so many warps with
+// short ranges win (down to TS_FUSED_MIN_PAIRS).  Once a grid has enough
+// work for TS_FUSED_FILL_WARPS_PER_SM warps per SM at that length, more
+// warps only add fills, so the floor grows with the work (up to
+// TS_FUSED_MAX_MIN_PAIRS).
+inline int64_t min_pairs_per_warp(int64_t units, int num_sms)
+{
+    const int64_t by_work = units / ((int64_t)TS_FUSED_FILL_WARPS_PER_SM * num_sms);
+    return std::min<int64_t>(TS_FUSED_MAX_MIN_PAIRS, std::max<int64_t>(TS_FUSED_MIN_PAIRS, by_work));
+}
+
 template <typename F>
 Occupancy occupancy_of(F kernel, int threads, int smem)
 {
@@ -1025,14 +1047,15 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.n_strips = (a.nx + C::VALID - 1) / C::VALID;
     p.n_pairs = (a.ny + 1) / 2;
     p.units = (int64_t)p.n_strips * p.n_pairs;
-    // at least ~16 row pairs per warp, at most the resident warps
-    int64_t want = (p.units + 15) / 16;
+    // at most the resident warps, each with at least min_pairs_per_warp row pairs
+    const int64_t mp = min_pairs_per_warp(p.units, num_sms);
+    int64_t want = (p.units + mp - 1) / mp;
     int64_t cap = (int64_t)num_sms * blocks_per_sm * C::WPC;
     p.total_warps = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     p.strip_warps = 0;
     if (TS_FUSED_ALIGNED && p.n_strips <= cap) {
         int64_t w = cap / p.n_strips;
-        const int64_t rows_cap = (p.n_pairs + 15) / 16;
+        const int64_t rows_cap = (p.n_pairs + mp - 1) / mp;
         if (w > rows_cap) w = rows_cap;
         if (w < 1) w = 1;
         p.strip_warps = (int)w;
@@ -1109,11 +1132,13 @@ cudaError_t launch_multi_k(const EpochEntry *tab, int n_grids, const MultiPlan &
     return cudaGetLastError();
 }
 
+// Resident warps of the multi-grid kernel at depth K (-1 on an error) and the SM count.
 template <int K>
-int64_t multi_capacity()
+int64_t multi_capacity(int &num_sms)
 {
     const Occupancy &occ = multi_occupancy<K>();
     if (occ.err != cudaSuccess) return -1;
+    num_sms = occ.num_sms;
     return (int64_t)occ.num_sms * occ.blocks_per_sm * Cfg<K>::WPC;
 }
 
@@ -1153,15 +1178,16 @@ MultiPlan fused_multi_plan(int K, int n, const int *nx, const int *ny, EpochEntr
 {
     MultiPlan plan = {0, 0, false};
     int64_t cap;
+    int num_sms = 1;
     switch (K) {
-    case 1: cap = multi_capacity<1>(); break;
-    case 2: cap = multi_capacity<2>(); break;
-    case 3: cap = multi_capacity<3>(); break;
-    case 4: cap = multi_capacity<4>(); break;
-    case 5: cap = multi_capacity<5>(); break;
-    case 6: cap = multi_capacity<6>(); break;
-    case 7: cap = multi_capacity<7>(); break;
-    case 8: cap = multi_capacity<8>(); break;
+    case 1: cap = multi_capacity<1>(num_sms); break;
+    case 2: cap = multi_capacity<2>(num_sms); break;
+    case 3: cap = multi_capacity<3>(num_sms); break;
+    case 4: cap = multi_capacity<4>(num_sms); break;
+    case 5: cap = multi_capacity<5>(num_sms); break;
+    case 6: cap = multi_capacity<6>(num_sms); break;
+    case 7: cap = multi_capacity<7>(num_sms); break;
+    case 8: cap = multi_capacity<8>(num_sms); break;
     default: return plan;
     }
     if (cap < 1 || n < 1) return plan;
@@ -1174,8 +1200,10 @@ MultiPlan fused_multi_plan(int K, int n, const int *nx, const int *ny, EpochEntr
         units += strips[(size_t)i] * pairs[(size_t)i];
         all_strips += strips[(size_t)i];
     }
-    // even split: at least ~16 row pairs per warp, at most the resident warps
-    const int64_t lin_warps = std::min(cap, std::max<int64_t>(1, (units + 15) / 16));
+    // even split: at most the resident warps, each with at least
+    // min_pairs_per_warp row pairs
+    const int64_t mp = min_pairs_per_warp(units, num_sms);
+    const int64_t lin_warps = std::min(cap, std::max<int64_t>(1, (units + mp - 1) / mp));
     const int64_t lin_span = (units + lin_warps - 1) / lin_warps;
     // aligned split: one warp per strip to start with, then more warps (on
     // every strip of a grid at once) to the grid with the most row pairs per
@@ -1188,7 +1216,7 @@ MultiPlan fused_multi_plan(int K, int n, const int *nx, const int *ny, EpochEntr
         for (int i = 0; i < n; ++i) heap.push({work(i), i});
         while (!heap.empty()) {
             const int i = heap.top().second;
-            if (al_warps + strips[(size_t)i] > cap || pairs[(size_t)i] / (w[(size_t)i] + 1) < 16)
+            if (al_warps + strips[(size_t)i] > cap || pairs[(size_t)i] / (w[(size_t)i] + 1) < mp)
                 break;
             heap.pop();
             ++w[(size_t)i];
