@@ -24,6 +24,7 @@
 #include "ffloat.cuh"
 #include "grid.h"
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -117,6 +118,7 @@ ts_status ts_adjoint_forward(ts_grid *g, const void *target_re, const void *targ
                              int64_t ckpt_every, void *ws, size_t ws_bytes, double *fidelity,
                              double *overlap, void *stream)
 {
+    ts::TraceRange trace_("ts_adjoint_forward");
     if (!g || !target_re || !target_im || !ws || !fidelity)
         return err(TS_ERR_ARG, "ts_adjoint_forward: null argument");
     if (g->f64()) return err(TS_ERR_UNSUPPORTED, "ts_adjoint_forward: FP32 grids only");
@@ -202,6 +204,7 @@ ts_status ts_adjoint_forward(ts_grid *g, const void *target_re, const void *targ
 
 ts_status ts_adjoint_backward(ts_grid *g, void *ws, size_t ws_bytes, float *grad, void *stream)
 {
+    ts::TraceRange trace_("ts_adjoint_backward");
     if (!g || !ws || !grad) return err(TS_ERR_ARG, "ts_adjoint_backward: null argument");
     AdjointState a;
     {

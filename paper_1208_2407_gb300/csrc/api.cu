@@ -14,6 +14,7 @@
 #include "../../include/trotter.h"
 #include "grid.h"
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -390,6 +391,7 @@ ts_status check_errword(ts_grid *g, cudaStream_t st)
 ts_status ts_set_state(ts_grid *g, const void *re, const void *im, ts_dtype src_dtype,
                        ts_mem where, void *stream)
 {
+    ts::TraceRange trace_("ts_set_state");
     if (!g || !re || !im) return fail(TS_ERR_ARG, "ts_set_state: null argument");
     if (src_dtype != TS_F32 && src_dtype != TS_F64)
         return fail(TS_ERR_ARG, "ts_set_state: unknown dtype");
@@ -430,6 +432,7 @@ ts_status ts_set_state(ts_grid *g, const void *re, const void *im, ts_dtype src_
 ts_status ts_get_state(ts_grid *g, void *re, void *im, ts_dtype dst_dtype, ts_mem where,
                        void *stream)
 {
+    ts::TraceRange trace_("ts_get_state");
     if (!g || !re || !im) return fail(TS_ERR_ARG, "ts_get_state: null argument");
     if (dst_dtype != TS_F32 && dst_dtype != TS_F64)
         return fail(TS_ERR_ARG, "ts_get_state: unknown dtype");
@@ -484,6 +487,7 @@ ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
 ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, double dt,
                                  double theta, int order, void *stream)
 {
+    ts::TraceRange trace_("ts_set_potential_order");
     if (!g) return fail(TS_ERR_ARG, "ts_set_potential: grid is NULL");
     if (!std::isfinite(dt) || !std::isfinite(theta))
         return fail(TS_ERR_ARG, "ts_set_potential: dt and theta must be finite");
@@ -551,6 +555,7 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
 ts_status ts_set_drive(ts_grid *g, const double *V1, ts_mem where, const double *a, int64_t n_a,
                        void *stream)
 {
+    ts::TraceRange trace_("ts_set_drive");
     if (!g) return fail(TS_ERR_ARG, "ts_set_drive: grid is NULL");
     if (n_a < 0 || (n_a > 0 && !a)) return fail(TS_ERR_ARG, "ts_set_drive: bad amplitude array");
     if (where != TS_HOST && where != TS_DEVICE)
@@ -929,6 +934,7 @@ ts_status evolve_f64(ts_grid *g, int64_t steps, cudaStream_t st)
 
 ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
 {
+    ts::TraceRange trace_("ts_evolve");
     if (!g) return fail(TS_ERR_ARG, "ts_evolve: grid is NULL");
     if (steps < 0) return fail(TS_ERR_ARG, "ts_evolve: negative step count");
     if (K < 0 || K > ts::FUSED_MAX_K) return fail(TS_ERR_ARG, "ts_evolve: K must be in [0, 8]");
@@ -973,6 +979,7 @@ ts_status ts_check_wait_timeout(ts_grid *g, int64_t limit_ns, void *stream)
 
 ts_status ts_evolve_plain(ts_grid *g, int64_t steps, void *stream)
 {
+    ts::TraceRange trace_("ts_evolve_plain");
     if (!g) return fail(TS_ERR_ARG, "ts_evolve_plain: grid is NULL");
     if (steps < 0) return fail(TS_ERR_ARG, "ts_evolve_plain: negative step count");
     if (steps == 0) return TS_OK;
@@ -983,6 +990,7 @@ ts_status ts_evolve_plain(ts_grid *g, int64_t steps, void *stream)
 
 ts_status ts_evolve_batched(ts_grid *const *gs, int n, const int64_t *steps, int K, void *stream)
 {
+    ts::TraceRange trace_("ts_evolve_batched");
     if (n < 0 || (n > 0 && (!gs || !steps))) return fail(TS_ERR_ARG, "ts_evolve_batched: bad arguments");
     if (K < 0 || K > ts::FUSED_MAX_K) return fail(TS_ERR_ARG, "ts_evolve_batched: K must be in [0, 8]");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1037,6 +1045,7 @@ ts_status observe(ts_grid *g, bool norm_only, double *res, cudaStream_t st)
 
 ts_status ts_observe(ts_grid *g, ts_observables *out, void *stream)
 {
+    ts::TraceRange trace_("ts_observe");
     if (!g || !out) return fail(TS_ERR_ARG, "ts_observe: null argument");
     double r[ts::OBS_Q3];
     ts_status s = observe(g, false, r, (cudaStream_t)stream);
@@ -1056,6 +1065,7 @@ ts_status ts_observe(ts_grid *g, ts_observables *out, void *stream)
 
 ts_status ts_norm(ts_grid *g, double *out, void *stream)
 {
+    ts::TraceRange trace_("ts_norm");
     if (!g || !out) return fail(TS_ERR_ARG, "ts_norm: null argument");
     double r[ts::OBS_Q3];
     ts_status s = observe(g, true, r, (cudaStream_t)stream);

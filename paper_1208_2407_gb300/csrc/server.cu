@@ -30,6 +30,7 @@
 #include "../../include/trotter.h"
 #include "grid.h"
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -174,6 +175,7 @@ cudaError_t ts_server::launch_full(int slot, int n, const ts::MultiPlan &plan, i
 // Allocate and fill one admitted request's grid on the copy stream.
 bool ts_server::admit_one(const ReqP &q)
 {
+    ts::TraceRange trace_("server admit");
     const ts_request &r = q->r;
     ts_layout L;
     ts_grid_layout(r.nx, r.ny, TS_F32, &L);
@@ -279,6 +281,7 @@ void ts_server::retire(Epoch &e, bool ok)
 // held; releases it around CUDA calls that may block).
 void ts_server::enqueue_epoch(std::unique_lock<std::mutex> &lk)
 {
+    ts::TraceRange trace_("server epoch");
     std::vector<ReqP> run_full, run_rem;
     for (auto &q : active) {
         if (q->cancel) continue;
