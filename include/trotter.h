@@ -112,8 +112,10 @@ ts_status ts_grid_info(const ts_grid *g, ts_layout *layout, void **re, void **im
  * memory (nx*ny elements each).  FP64 input to an FP32 grid is rounded once
  * to nearest on the device.  Host input is staged through the grid's own
  * ping-pong planes, so no extra device memory is used.  Async for device
- * input; for host input the copy is issued on `stream` and the call returns
- * when the host buffer may be reused. */
+ * input; for host input the copies are issued on `stream` and the call
+ * returns once they have landed (the host buffer may then be reused), while
+ * any conversion kernel stays queued on `stream`.  Work on the grid that
+ * follows on another stream must be ordered after it by the caller. */
 ts_status ts_set_state(ts_grid *g, const void *re, const void *im,
                        ts_dtype src_dtype, ts_mem where, void *stream);
 
@@ -132,8 +134,9 @@ ts_status ts_get_state(ts_grid *g, void *re, void *im, ts_dtype dst_dtype,
  * grids, within one ulp of the FP64 value rounded) and rounded once to the
  * grid's dtype.  The kinetic coefficients (1 - cos theta, sin theta,
  * tan(theta/2), and those of 2 theta for merged sweeps) are computed in
- * FP64 on the host and rounded once.  Async (host V: returns when V may be
- * reused). */
+ * FP64 on the host and rounded once.  Async; with host V the call returns
+ * once V has been copied to the device (V may then be reused) and the table
+ * kernels stay queued on `stream`. */
 ts_status ts_set_potential(ts_grid *g, const double *V, ts_mem where, double dt,
                            double theta, void *stream);
 

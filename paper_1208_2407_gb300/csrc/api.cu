@@ -74,6 +74,7 @@ ts_status grid_setup(const ts_layout &L, void *slab, bool owns_slab, ts_grid **o
     g->result = (double *)scr;
     scr += round_up(sizeof(double) * OBS_Q3, 256);
     g->err = (int *)scr;
+    g->host_copied = nullptr;
     scr += 256;
     g->desc_dev = (GridDesc *)scr;
     g->cur = 0;
@@ -337,6 +338,7 @@ ts_status ts_destroy_grid(ts_grid *g)
         cudaError_t f = cudaFree(extra);
         if (e == cudaSuccess) e = f;
     }
+    if (g->host_copied) cudaEventDestroy(g->host_copied);
     delete g;
     if (e != cudaSuccess) return cuda_fail(e, "ts_destroy_grid: cudaFree");
     return TS_OK;
@@ -355,7 +357,27 @@ namespace {
 
 // Copy a dense host array into the staging region (the two non-current
 // planes, contiguous in the slab) and convert it into `dst` on the device.
-ts_status stage_in(ts_grid *g, const void *host, ts_dtype src_dtype, void *dst, cudaStream_t st)
+// Wait until the host-to-device copies enqueued so far on `st` have landed,
+// so the caller's host buffer may be reused, without waiting for the kernels
+// that consume them: those stay queued in stream order.  (Waiting for the
+// whole stream would also wait for a table or conversion kernel that, on a
+// busy GPU, may sit behind another stream's higher-priority work.)
+ts_status wait_host_copies(ts_grid *g, cudaStream_t st, const char *who)
+{
+    cudaError_t e = cudaSuccess;
+    if (!g->host_copied) e = cudaEventCreateWithFlags(&g->host_copied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(g->host_copied, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(g->host_copied);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return TS_OK;
+}
+
+// The copy and the conversion are stream-ordered, so the region can be
+// staged into again by a later call on the same stream without a host wait.
+// With `copied`, the host waits for this copy to land (not for the
+// conversion) before the conversion is enqueued behind it.
+ts_status stage_in(ts_grid *g, const void *host, ts_dtype src_dtype, void *dst, cudaStream_t st,
+                   bool copied = false)
 {
     const size_t n = (size_t)g->L.nx * (size_t)g->rows();
     const size_t es = src_dtype == TS_F64 ? 8 : 4;
@@ -364,6 +386,10 @@ ts_status stage_in(ts_grid *g, const void *host, ts_dtype src_dtype, void *dst, 
     void *stage = g->re_other();
     cudaError_t e = cudaMemcpyAsync(stage, host, n * es, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    if (copied) {
+        ts_status s = wait_host_copies(g, st, "host-to-device copy");
+        if (s != TS_OK) return s;
+    }
     e = ts::launch_convert_in(stage, src_dtype == TS_F64, dst, g->f64(), (int)g->L.nx,
                               (int)g->rows(), g->L.pitch, st);
     if (e != cudaSuccess) return cuda_fail(e, "convert kernel");
@@ -414,19 +440,13 @@ ts_status ts_set_state(ts_grid *g, const void *re, const void *im, ts_dtype src_
         if (e == cudaSuccess)
             e = cudaMemcpy2DAsync(g->im(), g->L.pitch * es, im, nx * es, nx * es, ny,
                                   cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "ts_set_state: host-to-device copy");
-        return TS_OK;
+        return wait_host_copies(g, st, "ts_set_state: host-to-device copy");
     }
+    // both planes pass through the one staging region, in stream order
     ts_status s = stage_in(g, re, src_dtype, g->re(), st);
     if (s != TS_OK) return s;
-    cudaError_t e = cudaStreamSynchronize(st);   // staging region is reused next
-    if (e != cudaSuccess) return cuda_fail(e, "ts_set_state");
-    s = stage_in(g, im, src_dtype, g->im(), st);
-    if (s != TS_OK) return s;
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "ts_set_state");
-    return TS_OK;
+    return stage_in(g, im, src_dtype, g->im(), st, true);
 }
 
 ts_status ts_get_state(ts_grid *g, void *re, void *im, ts_dtype dst_dtype, ts_mem where,
@@ -537,6 +557,10 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
         const size_t n = (size_t)nx * ny;
         e = cudaMemcpyAsync(g->re_other(), V, n * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: host-to-device copy");
+        // V may be reused once it is on the device; the table kernels read the
+        // staged copy in stream order
+        ts_status s = wait_host_copies(g, st, "ts_set_potential: host-to-device copy");
+        if (s != TS_OK) return s;
         src = (const double *)g->re_other();
     }
     e = ts::launch_phase_table(src, g->pg(), g->ps(), g->vp(), g->f64(), nx, ny, g->L.pitch,
@@ -545,10 +569,6 @@ ts_status ts_set_potential_order(ts_grid *g, const double *V, ts_mem where, doub
         e = ts::launch_phase_table(src, g->pg_b(), g->ps_b(), g->vp(), g->f64(), nx, ny,
                                    g->L.pitch, w[1] * dt, st);
     if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential: table kernel");
-    if (where == TS_HOST) {
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(e, "ts_set_potential");
-    }
     return TS_OK;
 }
 
@@ -593,15 +613,13 @@ ts_status ts_set_drive(ts_grid *g, const double *V1, ts_mem where, const double 
             e = cudaMemcpyAsync(g->re_other(), V1, (size_t)nx * ny * sizeof(double),
                                 cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) return cuda_fail(e, "ts_set_drive: host-to-device copy");
+            ts_status s = wait_host_copies(g, st, "ts_set_drive: host-to-device copy");
+            if (s != TS_OK) return s;
             src = (const double *)g->re_other();
         }
         e = ts::launch_convert_in(src, true, g->drive_v1(), g->f64(), nx, ny, g->L.pitch, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "ts_set_drive: V1");
-    if (where == TS_HOST) {
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(e, "ts_set_drive");
-    }
     g->drive_a.assign(a, a + n_a);
     g->drive_pos = 0;
     g->driven = true;

@@ -45,6 +45,7 @@ struct ts_grid {
     bool driven;
     double *partials, *result;
     int *err;
+    cudaEvent_t host_copied;   // host-input copies done (created on first use)
     bool tmaps_ok;
     CUtensorMap tm_state[2], tm_phase;   // (re, im) of pair 0 / 1; (gamma_V, s_V)
     ts::GridDesc *desc_dev;              // the same, for multi-grid launches (in the slab)
