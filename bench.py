@@ -327,25 +327,24 @@ def serve_bench(n_requests: int, seed: int, budget_gb: float = 120.0):
 def e2e_bench(c, n, T, K, steps, warmup, dist, log=None, nbuf=2):
     """End to end through the C ABI with pinned host buffers.  Each step
     uploads psi (FP32) and V (FP64) from pinned host memory, runs the step and
-    reads the state and the observables back.  Two grids on two streams,
-    driven by two host threads (the ctypes calls release the GIL), let one
-    grid's copies overlap the other's kernels -- double buffering through the
-    same public calls a user makes.  `log`, if a list, receives (thread, step,
-    start, set_state, set_potential, evolve, get_state, observe) times."""
+    reads the state and the observables back.  Two grids on two streams make
+    a double buffer, driven by one host thread in a fixed order: while one
+    grid's kernels run, the other grid's result is read back and its next
+    inputs are uploaded.  Each grid's evolution waits (an event, on the
+    device) for the other grid's previous evolution, so the kernels of the two
+    grids alternate whole steps instead of sharing the SMs.  `log`, if a
+    list, receives (grid, step, start, get_state + observe of the previous
+    step, set_state, set_potential, evolve) host times."""
     import torch
     from paper_1208_2407_gb300 import trotter
     grids = [trotter.Grid(n, n, "f32") for _ in range(nbuf)]
-    # unequal priorities keep the two grids out of step: the first grid's
-    # kernels go first, and the second grid's copies overlap them (equal
-    # priorities measured 23.8 ms per step against 20.8 ms, kernels 19.3)
-    streams = [torch.cuda.Stream(priority=-1 if i == 0 else 0) for i in range(nbuf)]
+    streams = [torch.cuda.Stream() for _ in range(nbuf)]
     h_re = torch.from_numpy(c["re"].astype(np.float32)).pin_memory()
     h_im = torch.from_numpy(c["im"].astype(np.float32)).pin_memory()
     h_V = torch.from_numpy(c["V"]).pin_memory()
     outs = [(torch.empty((n, n), dtype=torch.float32).pin_memory(),
              torch.empty((n, n), dtype=torch.float32).pin_memory()) for _ in range(nbuf)]
     hp = lambda t: trotter._VP(t.data_ptr())
-    t_origin = [0.0]
     # the host link's speed on this box (pinned, one 256 MiB copy each way)
     probe = torch.empty(n * n, dtype=torch.float32, device="cuda")
     link = {}
@@ -359,61 +358,45 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None, nbuf=2):
         torch.cuda.synchronize()
         link[name] = round(4.0 * n * n / (a.elapsed_time(b) / 1e3) / 1e9, 1)
     del probe
+    sps = [trotter._VP(st.cuda_stream) for st in streams]
+    evolved = [torch.cuda.Event() for _ in range(nbuf)]   # after each grid's last evolve
 
-    # The grids' first uploads go one after another: grid i's wait for grid
-    # i - 1's on the device (otherwise they share the link and the first
-    # kernels start only after every grid's inputs are in).
-    first_up = [None] * nbuf
-    first_up_ready = [threading.Event() for _ in range(nbuf)]
-
-    def e2e_steps(i, count):
-        gh, sp_i = grids[i].handle, trotter._VP(streams[i].cuda_stream)
+    def read_back(i):
         o_re, o_im = outs[i]
+        trotter.ts_get_state(grids[i].handle, hp(o_re), hp(o_im), trotter.TS_F32,
+                             trotter.TS_HOST, sps[i])
+        trotter.ts_observe(grids[i].handle, sps[i])
+
+    def run_e2e(count, t_origin):
+        started = [False] * nbuf
+        last = None                       # the grid whose evolution was enqueued last
         for k in range(count):
-            if i > 0 and k == 0:
-                if not first_up_ready[i - 1].wait(120.0):
-                    raise RuntimeError("e2e: grid %d's first uploads never started" % (i - 1))
-                streams[i].wait_event(first_up[i - 1])
-            t = [time.perf_counter()]
-            trotter.ts_set_state(gh, hp(h_re), hp(h_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
-            t.append(time.perf_counter())
-            trotter.ts_set_potential(gh, hp(h_V), trotter.TS_HOST, c["dt"], c["theta"], sp_i)
-            t.append(time.perf_counter())
-            if k == 0:
-                first_up[i] = torch.cuda.Event()
-                first_up[i].record(streams[i])
-                first_up_ready[i].set()
-            trotter.ts_evolve(gh, T, K, sp_i)
-            t.append(time.perf_counter())
-            trotter.ts_get_state(gh, hp(o_re), hp(o_im), trotter.TS_F32, trotter.TS_HOST, sp_i)
-            t.append(time.perf_counter())
-            trotter.ts_observe(gh, sp_i)
-            t.append(time.perf_counter())
-            if log is not None:
-                log.append((i, k, t[0] - t_origin[0]) + tuple(t[m + 1] - t[m] for m in range(5)))
+            for i in range(nbuf):
+                t = [time.perf_counter()]
+                if started[i]:
+                    read_back(i)          # step k - 1 of grid i
+                t.append(time.perf_counter())
+                gh = grids[i].handle
+                trotter.ts_set_state(gh, hp(h_re), hp(h_im), trotter.TS_F32, trotter.TS_HOST,
+                                     sps[i])
+                t.append(time.perf_counter())
+                trotter.ts_set_potential(gh, hp(h_V), trotter.TS_HOST, c["dt"], c["theta"],
+                                         sps[i])
+                t.append(time.perf_counter())
+                if last is not None:
+                    streams[i].wait_event(evolved[last])
+                trotter.ts_evolve(gh, T, K, sps[i])
+                evolved[i].record(streams[i])
+                last, started[i] = i, True
+                t.append(time.perf_counter())
+                if log is not None:
+                    log.append((i, k, t[0] - t_origin) + tuple(t[m + 1] - t[m] for m in range(4)))
+        for i in range(nbuf):
+            j = (last + 1 + i) % nbuf     # the oldest evolution first
+            if started[j]:
+                read_back(j)
 
-    def run_e2e(per_worker):
-        for ev in first_up_ready:
-            ev.clear()
-        errors = []
-
-        def worker(i):
-            try:
-                e2e_steps(i, per_worker)
-            except BaseException as exc:      # re-raised below, in the caller
-                errors.append(exc)
-                for ev in first_up_ready:
-                    ev.set()
-
-        ths = [threading.Thread(target=worker, args=(i,)) for i in range(nbuf)]
-        for t in ths:
-            t.start()
-        for t in ths:
-            t.join()
-        if errors:
-            raise errors[0]
-
-    run_e2e(max(1, warmup // 2))
+    run_e2e(max(1, warmup // nbuf), time.perf_counter())
     torch.cuda.synchronize()
     dist.barrier()
     # at least 8 steps: the pipeline's fill (the first uploads) and drain (the
@@ -421,8 +404,8 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None, nbuf=2):
     per = max((8 + nbuf - 1) // nbuf, (steps + nbuf - 1) // nbuf)
     if log is not None:
         log.clear()
-    t0 = t_origin[0] = time.perf_counter()
-    run_e2e(per)
+    t0 = time.perf_counter()
+    run_e2e(per, t0)
     torch.cuda.synchronize()
     e2e_value = replica_throughput(dist, float(n) * n * T * per * nbuf, time.perf_counter() - t0)
     for gg in grids:
@@ -430,9 +413,9 @@ def e2e_bench(c, n, T, K, steps, warmup, dist, log=None, nbuf=2):
     return {"value": e2e_value, "unit": UNIT,
             "h2d_bytes_per_step": int(n * n * (4 + 4 + 8)),
             "d2h_bytes_per_step": int(n * n * (4 + 4) + 7 * 8),
-            "pipeline": "%d grids on %d streams (high and normal priority), one host "
-                        "thread each; each grid's first uploads wait for the previous "
-                        "grid's" % (nbuf, nbuf),
+            "pipeline": "%d grids on %d streams, one host thread; a grid's read-back and next "
+                        "uploads overlap the other grid's kernels, whose steps alternate"
+                        % (nbuf, nbuf),
             "steps": per * nbuf, "link": link}
 
 
