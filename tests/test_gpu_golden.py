@@ -1,7 +1,6 @@
 """The 256^2 workload on the GPU against the stored values in tests/golden/
 (written from the FP64 oracle): FP64 grids on both of their sequences to
 FP64 rounding, FP32 grids on the fused path to FP32 rounding."""
-import numpy as np
 import pytest
 
 from paper_1208_2407_gb300 import workloads as wl

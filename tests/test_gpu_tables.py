@@ -12,7 +12,7 @@ import pytest
 
 from paper_1208_2407_gb300 import trotter
 
-from gpu_helpers import ensure_library, grid_plane, random_state, rel_l2, run_gpu
+from gpu_helpers import ensure_library, grid_plane, random_state, run_gpu
 
 pytestmark = pytest.mark.gpu
 
