@@ -194,6 +194,13 @@ def oracle_sample(n: int, seed: int, budget_s: float = 12.0, max_steps: int = 10
         n, n, steps, TROTTER_STEPS, cores)
 
 
+def workload_config(n: int, T: int) -> dict:
+    """The workload both arms report: the n x n roofline grid, T steps per bench step."""
+    return {"workload": "roofline grid %dx%d, 32-Gaussian V, seed-random packet, %d Trotter "
+                        "steps per step" % (n, n, T),
+            "n": n, "trotter_steps_per_step": T}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -217,14 +224,14 @@ def run_reference(args):
     el = time.perf_counter() - t0
     value = n * n * per * args.steps / el
     sample = "%dx%d FP64 oracle, %d Trotter steps per step (bounded sample of %d), %d threads" % (
-        n, n, per, TROTTER_STEPS, cores)
+        n, n, per, args.trotter_steps, cores)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "roofline grid %dx%d, 32-Gaussian V, packet, FP64 CPU oracle" % (n, n),
-                   "n": n, "trotter_steps_per_step": per, "parallelism": "host threads"},
+        "config": dict(workload_config(n, args.trotter_steps), parallelism="host threads",
+                       sample_steps_per_step=per),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -574,11 +581,9 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "roofline grid %dx%d FP32, 32-Gaussian V, seed-random packet, "
-                                   "%d Trotter steps per step" % (n, n, T),
-                       "n": n, "trotter_steps_per_step": T, "K": k_eff,
-                       "l2": "inputs larger than L2 (%.1f GB working set)" % (n * n * 28 / 1e9),
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": dict(workload_config(n, T), K=k_eff,
+                           l2="inputs larger than L2 (%.1f GB working set)" % (n * n * 28 / 1e9),
+                           parallelism="replicas" if world > 1 else "single"),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
