@@ -68,3 +68,24 @@ def test_layout_and_argument_errors_without_gpu(lib):
     out = ctypes.c_double()
     assert lib.ts_norm(None, ctypes.byref(out), None) == trotter.TS_ERR_ARG
     assert "null" in trotter.ts_last_error()
+
+
+def declared_arity(path=HEADER):
+    """Parameter count of every ts_* function the header declares."""
+    text = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(ts_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else len(params.split(","))
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    """ctypes passes arguments blindly: a count that drifts from the C
+    declaration would pass garbage, so the binding's signature table must
+    agree with the header for every function it binds."""
+    from paper_1208_2407_gb300 import trotter
+    arity = declared_arity()
+    wrong = {name: (len(args), arity[name]) for name, args in trotter._SIGNATURES.items()
+             if name in arity and len(args) != arity[name]}
+    assert not wrong, wrong
