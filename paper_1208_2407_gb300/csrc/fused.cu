@@ -35,8 +35,12 @@
 // pair whose partner lies outside the grid gets coefficients (0, 0), i.e. the
 // identity (open boundaries: the unpaired site is unchanged).
 //
-// Work split: a persistent launch of P warps; the (strip, row-pair) units
-// are cut into P equal contiguous ranges, so all warps finish together.
+// Work split: a persistent launch gives each strip the same number of warps,
+// each on one row range, the same ranges in every strip, so that warps of
+// neighbouring strips walk the same rows together and share their halo
+// columns through L2 (min_pairs_per_warp sets how short a range may be).  The
+// multi-grid kernel picks between that split and an even split of all its
+// grids' (strip, row-pair) units (fused_multi_plan).
 //
 // Every wait on an mbarrier is bounded (globaltimer): on a timeout the warp
 // sets an error bit, waits (bounded) for its own outstanding copies and
