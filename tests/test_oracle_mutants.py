@@ -1,7 +1,7 @@
 """Planted mistakes: each mutant of the oracle source must fail at least one
 pin of test_oracle_pins.py.  This shows the pins constrain every part of the
-oracle (sign, angle, parity, axes, the phase and its place, the adjoint, the
-energy, the compensated sum).  Mutants are compiled on the CPU from edited
+oracle (sign, angle, parity, axes, the phase and its place, the fourth-order
+coefficients and their order, the adjoint, the energy, the compensated sum).  Mutants are compiled on the CPU from edited
 copies of oracle/trotter_oracle.c; the built oracle is restored afterwards."""
 import ctypes
 import os
@@ -52,6 +52,9 @@ MUTANTS = [
      "    for (int axis = 1; axis >= 0; --axis)"),
     ("z_pair_one_row_apart", "            rotate_pair(q->re, q->im, z * plane + i, (z + 1) * plane + i, q->c, q->s);",
      "            if (z * plane + i + q->nx < q->nx * q->ny * q->nz) rotate_pair(q->re, q->im, z * plane + i, z * plane + i + q->nx, q->c, q->s);"),
+    ("fourth_order_wrong_p", "    double p = 1.0 / (4.0 - cbrt(4.0));\n", "    double p = 0.4;\n"),
+    ("fourth_order_b_substep_first", "    double w[5] = {p, p, 1.0 - 4.0 * p, p, p};",
+     "    double w[5] = {1.0 - 4.0 * p, p, p, p, p};"),
     ("uncompensated_sum", "    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;\n    else a->c += (v - t) + a->s;\n",
      ""),
 ]
@@ -61,6 +64,7 @@ PIN_CHECKS = [
     lambda: [pins.test_single_sweep_equals_block_exponential(a, p) for a in "xy" for p in (0, 1)],
     pins.test_phase_equals_diagonal_exponential,
     pins.test_second_order_error_scaling,
+    pins.test_fourth_order_error_scaling,
     pins.test_flipped_sign_fails_exact_propagator,
     pins.test_time_reversal,
     pins.test_flat_potential_global_phase,
