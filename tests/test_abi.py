@@ -89,3 +89,15 @@ def test_binding_argument_counts_match_the_header():
     wrong = {name: (len(args), arity[name]) for name, args in trotter._SIGNATURES.items()
              if name in arity and len(args) != arity[name]}
     assert not wrong, wrong
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    """No CPU fallback: with the library missing, every entry into the
+    product path raises instead of computing anything."""
+    from paper_1208_2407_gb300 import trotter
+    monkeypatch.setattr(trotter, "_lib", None)
+    monkeypatch.setattr(trotter, "LIB_PATH", str(tmp_path / "libtrotter.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        trotter.load()
+    with pytest.raises(RuntimeError, match="not built"):
+        trotter.ts_grid_layout(64, 64, trotter.TS_F32)
