@@ -443,9 +443,15 @@ class Grid:
         ts_clear_drive(self.handle)
 
     def evolve(self, steps: int, K: int = 0, stream=None):
+        """`steps` steps (ts_evolve).  FP32 grids: the fused kernel at depth K
+        (0: the library's default).  FP64 grids: one sweep per launch with
+        the sweeps merged where steps meet (K must be 0).  Async."""
         ts_evolve(self.handle, int(steps), int(K), stream or current_stream_ptr())
 
     def evolve_plain(self, steps: int, stream=None):
+        """`steps` steps one sweep per launch, the literal sequence
+        (ts_evolve_plain): the reference point the other paths are measured
+        against.  Async."""
         ts_evolve_plain(self.handle, int(steps), stream or current_stream_ptr())
 
     def observe(self, stream=None) -> dict:
