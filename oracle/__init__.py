@@ -65,8 +65,6 @@ def bind(lib):
         "oracle_inner": [_I64, _DP, _DP, _DP, _DP, _DP],
         "oracle_adjoint_grad": [_I64, _I64, _DP, _DP, _DP, _DP, _DP, ctypes.c_double,
                                 ctypes.c_double, _I64, _DP, _DP, _DP, ctypes.c_int],
-        "oracle_apply_A": [_I64, _I64, _DP, _DP, ctypes.c_double, ctypes.c_int],
-        "oracle_apply_B": [_I64, _I64, _DP, _DP, ctypes.c_double, ctypes.c_int],
         "oracle_compensated_sum": [_I64, _DP],
     }
     for name, args in sig.items():
@@ -74,9 +72,8 @@ def bind(lib):
     for name in ("oracle_evolve", "oracle_evolve_driven", "oracle_evolve3", "oracle_adjoint_grad"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("oracle_sweep_x", "oracle_sweep_y", "oracle_phase", "oracle_step2",
-                 "oracle_moments", "oracle_energy", "oracle_inner", "oracle_apply_A",
-                 "oracle_sweep3", "oracle_moments3", "oracle_energy3",
-                 "oracle_apply_B"):
+                 "oracle_moments", "oracle_energy", "oracle_inner",
+                 "oracle_sweep3", "oracle_moments3", "oracle_energy3"):
         getattr(lib, name).restype = None
     lib.oracle_compensated_sum.restype = ctypes.c_double
     return lib
@@ -269,22 +266,6 @@ def adjoint_grad(psi0_re, psi0_im, phi_re, phi_im, V, dt: float, theta: float,
     if rc != 0:
         raise RuntimeError("oracle_adjoint_grad failed (rc=%d)" % rc)
     return grad, float(fid[0]), complex(ov[0], ov[1])
-
-
-def apply_A(re, im, theta: float):
-    lib = _load()
-    re, im = _state(re, im)
-    ny, nx = re.shape
-    lib.oracle_apply_A(nx, ny, _ptr(re), _ptr(im), float(theta), 1)
-    return re, im
-
-
-def apply_B(re, im, theta: float):
-    lib = _load()
-    re, im = _state(re, im)
-    ny, nx = re.shape
-    lib.oracle_apply_B(nx, ny, _ptr(re), _ptr(im), float(theta), 1)
-    return re, im
 
 
 def compensated_sum(v) -> float:

@@ -478,24 +478,6 @@ void oracle_inner(int64_t n, const double *are, const double *aim,
 /* trajectory); the test-suite pins the result against finite differences   */
 /* of the forward evolution.                                                  */
 /* ------------------------------------------------------------------------ */
-static void apply_A(int64_t nx, int64_t ny, double *re, double *im,
-                    double theta, int nthreads)
-{
-    oracle_sweep_x(nx, ny, re, im, 0, theta, nthreads);
-    oracle_sweep_x(nx, ny, re, im, 1, theta, nthreads);
-    oracle_sweep_y(nx, ny, re, im, 0, theta, nthreads);
-    oracle_sweep_y(nx, ny, re, im, 1, theta, nthreads);
-}
-
-static void apply_B(int64_t nx, int64_t ny, double *re, double *im,
-                    double theta, int nthreads)
-{
-    oracle_sweep_y(nx, ny, re, im, 1, theta, nthreads);
-    oracle_sweep_y(nx, ny, re, im, 0, theta, nthreads);
-    oracle_sweep_x(nx, ny, re, im, 1, theta, nthreads);
-    oracle_sweep_x(nx, ny, re, im, 0, theta, nthreads);
-}
-
 /* B^dagger: the factors of B in reverse order, each at -theta. */
 static void apply_B_dag(int64_t nx, int64_t ny, double *re, double *im,
                         double theta, int nthreads)
@@ -575,19 +557,6 @@ int oracle_adjoint_grad(int64_t nx, int64_t ny, const double *psi0_re,
     free(acc);
     free(pr); free(pi); free(lr); free(li); free(Vneg);
     return 0;
-}
-
-/* Forward helpers exposed for the adjoint pins: apply A, P, B separately. */
-void oracle_apply_A(int64_t nx, int64_t ny, double *re, double *im,
-                    double theta, int nthreads)
-{
-    apply_A(nx, ny, re, im, theta, nthreads);
-}
-
-void oracle_apply_B(int64_t nx, int64_t ny, double *re, double *im,
-                    double theta, int nthreads)
-{
-    apply_B(nx, ny, re, im, theta, nthreads);
 }
 
 /* Neumaier-compensated sum of an array (exposed so that its own pin can

@@ -1,8 +1,9 @@
 """Planted mistakes: each mutant of the oracle source must fail at least one
 pin of test_oracle_pins.py.  This shows the pins constrain every part of the
 oracle (sign, angle, parity, axes, the phase and its place, the fourth-order
-coefficients and their order, the adjoint, the energy, the compensated sum).  Mutants are compiled on the CPU from edited
-copies of oracle/trotter_oracle.c; the built oracle is restored afterwards."""
+coefficients and their order, the adjoint, the energy, the compensated sum,
+the threaded row split).  Mutants are compiled on the CPU from edited copies
+of oracle/trotter_oracle.c; the built oracle is restored afterwards."""
 import ctypes
 import os
 import subprocess
@@ -14,6 +15,7 @@ import oracle
 import test_oracle_3d as three
 import test_oracle_drive as drive
 import test_oracle_pins as pins
+import test_oracle_threads as threads
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "trotter_oracle.c")
 
@@ -55,6 +57,8 @@ MUTANTS = [
     ("fourth_order_wrong_p", "    double p = 1.0 / (4.0 - cbrt(4.0));\n", "    double p = 0.4;\n"),
     ("fourth_order_b_substep_first", "    double w[5] = {p, p, 1.0 - 4.0 * p, p, p};",
      "    double w[5] = {1.0 - 4.0 * p, p, p, p, p};"),
+    ("thread_chunk_skips_a_row", "        jobs[t].lo = n * t / nthreads;\n",
+     "        jobs[t].lo = n * t / nthreads + (t > 0);\n"),
     ("uncompensated_sum", "    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;\n    else a->c += (v - t) + a->s;\n",
      ""),
 ]
@@ -76,6 +80,7 @@ PIN_CHECKS = [
     drive.test_driven_steps_equal_dense_products,
     lambda: [three.test_step_equals_dense_product(*d) for d in [(2, 2, 2), (2, 3, 4)]],
     drive.test_uniform_drive_is_a_global_phase,
+    threads.check_all_splits,
 ]
 
 
