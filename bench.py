@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the FP32 / FP64 path comparison")
+    ap.add_argument("--no-k-sweep", action="store_true",
+                    help="skip the depth sweep (K = 1..8 at 8192^2 and 16384^2, plain paths)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--n3", type=int, default=512, help="side of the 3-D lattice in --variants")
     ap.add_argument("--only", choices=["order4", "drive", "3d"], default=None,
@@ -472,6 +474,80 @@ def precision_paths(c, n, fused_rate, reps=3, steps=10):
     return out
 
 
+# algorithmic bytes per site-step of the paths k_sweep times (state 8 B/site FP32,
+# 16 B FP64; the table gamma_V, s_V as wide as the state)
+PLAIN_BYTES = {"f32": 8 * 16 + 24, "f64": 16 * 16 + 48}   # 8 sweeps + the phase
+
+
+def fp64_merged_bytes(T: int) -> float:
+    """ts_evolve on an FP64 grid: 6 T + 2 sweeps (32 B/site each) and T phases
+    (48 B/site) for T steps, per site-step."""
+    return ((6 * T + 2) * 32 + T * 48) / T
+
+
+def k_sweep(args, hbm_peak, sizes=(8192, 16384), depths=range(1, 9), reps=3):
+    """The roofline sweep: for each grid side, 200 Trotter steps of the fused
+    kernel at every depth K = 1..8 (median of `reps` runs, CUDA events), then
+    the plain one-sweep-per-kernel FP32 and FP64 paths and FP64 ts_evolve (one
+    run each, 200 steps).  A fused launch moves 24 B per site whatever its
+    depth, so T steps at depth K move 24 B x sites x ceil(T / K)."""
+    import torch
+    from paper_1208_2407_gb300 import trotter
+    from paper_1208_2407_gb300 import workloads as wl
+    T = args.trotter_steps
+    rows = []
+
+    def timed(fn, count):
+        fn(1)
+        ms = []
+        for _ in range(count):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn(T)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sorted(ms)[len(ms) // 2]
+
+    for n in sizes:
+        c = wl.roofline_grid(n=n, seed=args.seed, steps=T)
+        sites = float(n) * n
+        for dtype in ("f32", "f64"):
+            tdt = torch.float32 if dtype == "f32" else torch.float64
+            g = trotter.Grid(n, n, dtype)
+            try:
+                g.set_state(torch.from_numpy(c["re"]).to(tdt).cuda(),
+                            torch.from_numpy(c["im"]).to(tdt).cuda())
+                g.set_potential(torch.from_numpy(c["V"]).cuda(), c["dt"], c["theta"])
+                paths = []
+                if dtype == "f32":
+                    for K in depths:
+                        launches = -(-T // K)
+                        paths.append(("fused", K, lambda m, K=K: g.evolve(m, K), reps,
+                                      24.0 * launches / T))
+                    paths.append(("plain", None, g.evolve_plain, 1, PLAIN_BYTES["f32"]))
+                else:
+                    paths.append(("plain", None, g.evolve_plain, 1, PLAIN_BYTES["f64"]))
+                    paths.append(("evolve", None, g.evolve, 1, fp64_merged_bytes(T)))
+                for path, K, fn, count, bps in paths:
+                    ms = timed(fn, count)
+                    rate = sites * T / (ms / 1e3)
+                    gbs = rate * bps / 1e9
+                    row = {"n": n, "dtype": dtype, "path": path, "K": K, "steps": T, "ms": ms,
+                           "site_steps_per_s": rate, "bytes_per_site_step": bps,
+                           "achieved_gbs": gbs, "frac": gbs / hbm_peak}
+                    if path == "fused":
+                        row["traffic_per_launch"] = recorded_traffic(n, K)
+                    rows.append(row)
+            finally:
+                g.close()
+        del c
+        torch.cuda.empty_cache()
+    return {"peak_gbs": hbm_peak, "rows": rows,
+            "note": "inputs resident in HBM; fused rows: median of %d runs; others: one run" % reps}
+
+
 def run_ours(args):
     import torch
     from paper_1208_2407_gb300 import trotter
@@ -570,6 +646,13 @@ def run_ours(args):
             g = None
         precision = precision_paths(c, n, site_steps * args.steps / (evolve_ms / 1e3))
 
+    ksweep = None
+    if rank == 0 and world == 1 and not args.no_k_sweep:
+        if g is not None:
+            g.close()
+            g = None
+        ksweep = k_sweep(args, hbm_peak)
+
     serve = None
     if rank == 0 and not args.no_serve:
         if g is not None:
@@ -598,6 +681,7 @@ def run_ours(args):
             "clocks": clocks,
             "obs_last": {"norm": obs["norm"], "energy": obs["e_kin"] + obs["e_pot"]},
             "precision": precision,
+            "k_sweep": ksweep,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)

@@ -367,6 +367,12 @@ ts_status ts_server_destroy(ts_server *s);
  * The reduction uses at most 1024 blocks, so any grid with sides in [1, 2^20]
  * fits; other sides, pitch < nx, null pointers or an unknown dtype return
  * TS_ERR_ARG with a message in ts_last_error().
+ * Alignment: FP32 planes are read 4 sites at a time with 16-byte loads, so
+ * for TS_F32 re and im must be 16-byte aligned and pitch a multiple of 4;
+ * for TS_F64 they must be 8-byte aligned.  Anything else returns TS_ERR_ARG
+ * before any kernel runs.  Each plane must span ny * pitch elements (the
+ * last row's padding included): the last 16-byte load of a row may read up
+ * to 3 floats past column nx - 1, never past the row's pitch.
  * The first call on each device looks the array's device address up (with
  * that device current); make that first call before any stream capture.
  * All calls share the one array: calls that overlap on the GPU (on different

@@ -10,6 +10,7 @@
 // name as a device address (on the host the name is only a stand-in); the
 // device address is looked up once per device with cudaGetSymbolAddress, with
 // that device current, and passed to the kernels.
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -51,6 +52,17 @@ extern "C" ts_status ts_norm_noalloc(const void *re, const void *im, ts_dtype dt
     if (pitch < nx || pitch > (int64_t(1) << 31))
         return (ts_status)ts::set_error(TS_ERR_ARG, "ts_norm_noalloc: pitch %lld must be in "
                                         "[nx, 2^31]", (long long)pitch);
+    // The FP32 reduction reads 4 sites at a time with 16-byte loads from
+    // re + y*pitch + x0 (x0 a multiple of 4), so the planes must be 16-byte
+    // aligned and the pitch a multiple of 4 floats; then a row's last load
+    // stays inside that row's pitch.  The FP64 reduction loads single doubles.
+    const uintptr_t align = dtype == TS_F32 ? 16 : 8;
+    if ((uintptr_t)re % align != 0 || (uintptr_t)im % align != 0)
+        return (ts_status)ts::set_error(TS_ERR_ARG, "ts_norm_noalloc: re and im must be %d-byte "
+                                        "aligned for this dtype", (int)align);
+    if (dtype == TS_F32 && pitch % 4 != 0)
+        return (ts_status)ts::set_error(TS_ERR_ARG, "ts_norm_noalloc: an FP32 pitch must be a "
+                                        "multiple of 4, got %lld", (long long)pitch);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return (ts_status)ts::set_error(TS_ERR_CUDA, "ts_norm_noalloc: no usable current device");

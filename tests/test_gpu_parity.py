@@ -133,18 +133,50 @@ def test_fused_matches_plain_fp32_on_a_packet(K):
 # ---------------------------------------------------------------------------
 # the 2048^2 FP32 precision workload, 1000 steps, vs the FP64 oracle
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("seed", [0, 1])
-def test_harmonic_2048_fp32_vs_fp64_oracle(seed):
+# Norm drift bound: the lifting and versine forms keep each sweep's defect
+# |c^2 + s^2 - 1| near 1e-10 (tables rounded once from FP64), so 1000 steps of
+# ~7 sweeps drift the norm by at most ~1e-6 even if every defect had one sign;
+# FP32 rounding itself is unbiased and adds ~1e-8.
+NORM_DRIFT_TOL = 1e-6
+# The energy of the Trotter map itself oscillates at O(dt^2), so the GPU's
+# energy drift is compared with the oracle's drift on the same packet: FP32
+# state errors of ~4e-6 rel-L2 move <psi|H|psi> by ~1e-5 of |E| at most.
+ENERGY_DRIFT_TOL = 2e-5
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4])
+def test_harmonic_2048_fp32_vs_fp64_oracle(seed, record_property):
     c = wl.harmonic_2048(seed=seed)
-    (gre, gim), obs = run_gpu(c["re"], c["im"], c["V"], c["dt"], c["theta"], c["steps"],
-                              observe=True)
+    g = trotter.Grid(c["nx"], c["ny"], "f32")
+    try:
+        g.set_state(c["re"], c["im"])
+        g.set_potential(c["V"], c["dt"], c["theta"])
+        obs0 = g.observe()
+        g.evolve(c["steps"])
+        obs = g.observe()
+        gre, gim = g.get_state(np.float64)
+    finally:
+        g.close()
     ore, oim = oracle.evolve(c["re"], c["im"], c["V"], c["dt"], c["theta"], c["steps"],
                              nthreads=NTHREADS)
     err = rel_l2(gre, gim, ore, oim)
     assert err < FP32_TOL, err
-    assert abs(obs["norm"] - 1.0) < 1e-5
-    kin, pot = oracle.energy(ore, oim, c["V"])
-    assert abs(obs["e_kin"] + obs["e_pot"] - (kin + pot)) < 1e-4 * max(1.0, abs(kin + pot))
+    norm_drift = abs(obs["norm"] - obs0["norm"])
+    assert norm_drift < NORM_DRIFT_TOL, norm_drift
+    e0 = sum(oracle.energy(c["re"], c["im"], c["V"]))
+    e_oracle = sum(oracle.energy(ore, oim, c["V"]))
+    e_gpu0 = obs0["e_kin"] + obs0["e_pot"]
+    e_gpu = obs["e_kin"] + obs["e_pot"]
+    scale = max(1e-12, abs(e0))
+    drift_gpu = (e_gpu - e_gpu0) / scale
+    drift_oracle = (e_oracle - e0) / scale
+    assert abs(drift_gpu - drift_oracle) < ENERGY_DRIFT_TOL, (drift_gpu, drift_oracle)
+    assert abs(e_gpu - e_oracle) < 1e-4 * max(1.0, abs(e_oracle))
+    for k, v in (("rel_l2", err), ("norm_drift", norm_drift), ("energy_drift_rel", drift_gpu),
+                 ("energy_drift_rel_oracle", drift_oracle), ("energy0", e0)):
+        record_property(k, v)
+    print("config 2 seed %d: rel-L2 %.3e, norm drift %.2e, energy drift %.3e (oracle %.3e)"
+          % (seed, err, norm_drift, drift_gpu, drift_oracle))
 
 
 # ---------------------------------------------------------------------------
