@@ -57,6 +57,8 @@ def parse():
                     help="skip the FP32 / FP64 path comparison")
     ap.add_argument("--no-k-sweep", action="store_true",
                     help="skip the depth sweep (K = 1..8 at 8192^2 and 16384^2, plain paths)")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint timing (1024^2 x 500 and 4096^2 x 200 steps)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--n3", type=int, default=512, help="side of the 3-D lattice in --variants")
     ap.add_argument("--only", choices=["order4", "drive", "3d"], default=None,
@@ -64,6 +66,16 @@ def parse():
     ap.add_argument("--variants", action="store_true",
                     help="time fourth-order steps and a time-dependent potential instead "
                          "(prints its own JSON line)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time only the adjoint on one --adj-n^2 grid (--adj-steps, --adj-ckpt; "
+                         "backward depth --K, 0 = depths 1..4; --steps runs each)")
+    ap.add_argument("--traffic", action="store_true",
+                    help="launch the fused kernel once per depth 1..8 on each --traffic-n side "
+                         "(after one warm-up launch each), for an ncu DRAM-traffic capture")
+    ap.add_argument("--traffic-n", type=int, nargs="+", default=[8192, 16384])
+    ap.add_argument("--adj-n", type=int, default=1024)
+    ap.add_argument("--adj-steps", type=int, default=500)
+    ap.add_argument("--adj-ckpt", type=int, default=50)
     ap.add_argument("--paper", action="store_true",
                     help="time the paper's single-node sizes instead (L = 24576 FP32, "
                          "17472 FP64, flat V, ten iterations)")
@@ -548,6 +560,100 @@ def k_sweep(args, hbm_peak, sizes=(8192, 16384), depths=range(1, 9), reps=3):
             "note": "inputs resident in HBM; fused rows: median of %d runs; others: one run" % reps}
 
 
+def adjoint_bytes(n_sites: int, steps: int, ckpt: int, K: int, K_fwd: int):
+    """Algorithmic bytes of one adjoint forward and one backward pass on an
+    FP32 grid (per site: a state 8 B, the table 8 B, G 16 B as double-float
+    re, im).  Forward: target conversion (16), per segment ts_evolve at depth
+    K_fwd (24 per launch) and a checkpoint copy (16), the overlap
+    <phi|psi_T> (16).  Backward: costate set-up (16), G cleared (16), per
+    segment a checkpoint copy (16) and launches of K backward steps on psi
+    and lambda together (72 per launch: both states read and written 32, the
+    table 8, G read and written 32), then the gradient (G 16 in, 4 out)."""
+    fwd, bwd = 16 + 16, 16 + 16 + 20
+    for s0 in range(0, steps, ckpt):
+        ns = min(ckpt, steps - s0)
+        fwd += 16 + 24 * -(-ns // K_fwd)
+        bwd += 16 + 72 * -(-ns // K)
+    return fwd * n_sites, bwd * n_sites
+
+
+def adjoint_bench(args, hbm_peak, cases=((1024, 500, 50), (4096, 200, 50)), depths=(1, 2, 3, 4),
+                  reps=3):
+    """The adjoint workload (config 5: 1024^2, 500 steps, checkpoints every
+    50) and a 4096^2 grid: CUDA-event time of ts_adjoint_forward and of
+    ts_adjoint_backward_depth at each depth (median of `reps`), with the
+    algorithmic bytes of each pass and its fraction of measured HBM."""
+    import torch
+    from paper_1208_2407_gb300 import trotter
+    from paper_1208_2407_gb300 import workloads as wl
+    out = []
+    K_fwd = trotter.ts_fused_default_depth()
+    for n, steps, ckpt in cases:
+        c = wl.adjoint_pair(n=n, steps=steps, seed=args.seed)
+        g = trotter.Grid(n, n, "f32")
+        try:
+            re0 = torch.from_numpy(c["re"].astype(np.float32)).cuda()
+            im0 = torch.from_numpy(c["im"].astype(np.float32)).cuda()
+            tre = torch.from_numpy(c["target_re"].astype(np.float32)).cuda()
+            tim = torch.from_numpy(c["target_im"].astype(np.float32)).cuda()
+            g.set_potential(torch.from_numpy(c["V"]).cuda(), c["dt"], c["theta"])
+            nbytes = trotter.ts_adjoint_workspace(g.handle, steps, ckpt)
+            ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            grad = torch.empty((n, n), dtype=torch.float32, device="cuda")
+            sp = trotter.current_stream_ptr()
+            wsp, gp = trotter._VP(ws.data_ptr()), trotter._VP(grad.data_ptr())
+
+            def ev_time(fn):
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                r = fn()
+                b.record()
+                torch.cuda.synchronize()
+                return a.elapsed_time(b), r
+
+            def forward():
+                return trotter.ts_adjoint_forward(
+                    g.handle, trotter._VP(tre.data_ptr()), trotter._VP(tim.data_ptr()),
+                    trotter.TS_F32, trotter.TS_DEVICE, steps, ckpt, wsp, nbytes, sp)[0]
+
+            row = {"n": n, "steps": steps, "ckpt": ckpt, "K_forward": K_fwd, "backward": []}
+            fw_ms = []
+            for K in depths:
+                bw_ms = []
+                for rep in range(reps + 1):
+                    g.set_state(re0, im0)
+                    ms, F = ev_time(forward)
+                    if rep:
+                        fw_ms.append(ms)
+                    ms, _ = ev_time(lambda: trotter.ts_adjoint_backward_depth(
+                        g.handle, wsp, nbytes, K, gp, sp))
+                    if rep:
+                        bw_ms.append(ms)
+                t = sorted(bw_ms)[len(bw_ms) // 2]
+                fb, bb = adjoint_bytes(n * n, steps, ckpt, K, K_fwd)
+                row["backward"].append({
+                    "K": K, "ms": t, "bytes": bb, "bytes_per_site_step": bb / (n * n * steps),
+                    "achieved_gbs": bb / (t / 1e3) / 1e9,
+                    "frac": bb / (t / 1e3) / 1e9 / hbm_peak})
+            tf = sorted(fw_ms)[len(fw_ms) // 2]
+            fb, _ = adjoint_bytes(n * n, steps, ckpt, 1, K_fwd)
+            row.update({"forward_ms": tf, "forward_bytes": fb,
+                        "forward_bytes_per_site_step": fb / (n * n * steps),
+                        "forward_achieved_gbs": fb / (tf / 1e3) / 1e9,
+                        "forward_frac": fb / (tf / 1e3) / 1e9 / hbm_peak, "fidelity": F})
+            best = min(row["backward"], key=lambda r: r["ms"])
+            row["best_backward_K"] = best["K"]
+            row["backward_over_forward"] = best["ms"] / tf
+            out.append(row)
+            del ws, grad
+        finally:
+            g.close()
+        torch.cuda.empty_cache()
+    return {"peak_gbs": hbm_peak, "cases": out,
+            "note": "inputs resident in HBM; median of %d runs per depth" % reps}
+
+
 def run_ours(args):
     import torch
     from paper_1208_2407_gb300 import trotter
@@ -653,6 +759,13 @@ def run_ours(args):
             g = None
         ksweep = k_sweep(args, hbm_peak)
 
+    adjoint = None
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        if g is not None:
+            g.close()
+            g = None
+        adjoint = adjoint_bench(args, hbm_peak)
+
     serve = None
     if rank == 0 and not args.no_serve:
         if g is not None:
@@ -682,6 +795,7 @@ def run_ours(args):
             "obs_last": {"norm": obs["norm"], "energy": obs["e_kin"] + obs["e_pot"]},
             "precision": precision,
             "k_sweep": ksweep,
+            "adjoint": adjoint,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)
@@ -842,8 +956,61 @@ def method_variants(args):
     return 0
 
 
+def traffic_launches(args):
+    """For an ncu capture of DRAM traffic (one pass, gpu__time_duration and
+    dram__bytes_{read,write}): on each grid side of the depth sweep, one
+    warm-up launch and then exactly one launch of the fused kernel at every
+    depth K = 1..8 (ts_evolve of K steps at depth K).  The kernel of launch
+    2i + 1 on side n is fused_kernel<i + 1>."""
+    import torch
+    from paper_1208_2407_gb300 import trotter
+    from paper_1208_2407_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    trotter.load()
+    for n in args.traffic_n:
+        c = wl.roofline_grid(n=n, seed=args.seed, steps=1)
+        g = trotter.Grid(n, n, "f32")
+        try:
+            g.set_state(torch.from_numpy(c["re"].astype(np.float32)).cuda(),
+                        torch.from_numpy(c["im"].astype(np.float32)).cuda())
+            g.set_potential(torch.from_numpy(c["V"]).cuda(), c["dt"], c["theta"])
+            for K in range(1, 9):
+                g.evolve(K, K)
+                g.evolve(K, K)
+            torch.cuda.synchronize()
+        finally:
+            g.close()
+        del c
+    print(json.dumps({"traffic_launches": list(args.traffic_n),
+                      "kernel_source_hash": kernel_source_hash()}), flush=True)
+    return 0
+
+
+def adjoint_only(args):
+    import torch
+    from paper_1208_2407_gb300 import trotter
+    torch.cuda.set_device(0)
+    trotter.load()
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    depths = (args.K,) if args.K > 0 else (1, 2, 3, 4)
+    r = adjoint_bench(args, float(peaks.get("hbm_gbs", 6800.0)),
+                      cases=((args.adj_n, args.adj_steps, args.adj_ckpt),), depths=depths,
+                      reps=max(1, args.steps))
+    print(json.dumps({"metric": "adjoint forward and backward", "adjoint": r}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.adjoint:
+        return adjoint_only(args)
+    if args.traffic:
+        return traffic_launches(args)
     if args.paper:
         return paper_sizes(args)
     if args.variants:

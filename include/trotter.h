@@ -255,11 +255,12 @@ ts_status ts_evolve_batched(ts_grid *const *g, int n, const int64_t *steps, int 
  * lambda_{s-1} = U_s^dagger lambda_s and m_s = P A psi_{s-1}:
  *   dF/dV_j = 2 dt Im( conj(c) sum_s conj((B^dagger lambda_s)[j]) m_s[j] ).
  * U^dagger is the step at -theta with the conjugate phase; the backward pass
- * runs it as a hand-written kernel and recomputes the m_s of each segment of
- * `ckpt_every` steps from a checkpoint of psi.  FP32 grids, |theta| <= pi/4.
+ * runs it as a hand-written kernel on lambda and on psi together (m_s is
+ * B^dagger psi_s), restarting psi from a checkpoint at the end of each
+ * segment of `ckpt_every` steps.  FP32 grids, |theta| <= pi/4.
  *
  * ts_adjoint_workspace: bytes of device workspace for (steps, ckpt_every):
- *   about (14 + 2 ceil(steps/ckpt) + 2 ckpt) planes of the grid.
+ *   about (14 + 2 ceil(steps/ckpt)) planes of the grid.
  * ts_adjoint_forward: target phi as dense arrays (host or device, FP32 or
  *   FP64); evolves the grid's state by `steps` (the grid then holds psi_T),
  *   keeps checkpoints in `ws` (caller-owned, 256-byte aligned), returns F
@@ -267,6 +268,10 @@ ts_status ts_evolve_batched(ts_grid *const *g, int n, const int64_t *steps, int 
  * ts_adjoint_backward: after a forward with the same ws, writes dF/dV as a
  *   dense nx*ny FP32 device array `grad`.  Syncs.  One forward/backward pair
  *   per grid at a time; TS_ERR_STATE without a matching forward.
+ *   psi and lambda step back together, K steps per fused launch (K = 2).
+ * ts_adjoint_backward_depth: the same with the depth K of those launches
+ *   given (1..4; 0 = the default); other K return TS_ERR_ARG.  K changes only
+ *   the order in which G's terms are summed, not the gradient it defines.
  * ts_adjoint_grad: forward then backward. */
 ts_status ts_adjoint_workspace(const ts_grid *g, int64_t steps, int64_t ckpt_every,
                                size_t *bytes);
@@ -275,6 +280,8 @@ ts_status ts_adjoint_forward(ts_grid *g, const void *target_re, const void *targ
                              int64_t ckpt_every, void *ws, size_t ws_bytes, double *fidelity,
                              double *overlap, void *stream);
 ts_status ts_adjoint_backward(ts_grid *g, void *ws, size_t ws_bytes, float *grad, void *stream);
+ts_status ts_adjoint_backward_depth(ts_grid *g, void *ws, size_t ws_bytes, int K, float *grad,
+                                    void *stream);
 ts_status ts_adjoint_grad(ts_grid *g, const void *target_re, const void *target_im,
                           ts_dtype target_dtype, ts_mem where, int64_t steps, int64_t ckpt_every,
                           void *ws, size_t ws_bytes, float *grad, double *fidelity, void *stream);

@@ -7,12 +7,22 @@
 // m_s = P A psi_{s-1} and lt_s = B^dagger lambda_s,
 //   dF/dV_j = 2 dt Im( conj(c) G_j ),   G_j = sum_s conj(lt_s[j]) m_s[j].
 // U^dagger is the same sweep sequence at -theta with the conjugate phase, and
-// lt_s is its state at the phase point, so a backward step is the fused K = 1
-// step at -theta with a hook there (fused.cu, mode 2).
+// lt_s is its state at the phase point.  The mid-step state is the forward
+// state's value at the same point, m_s = P A psi_{s-1} = B^dagger psi_s, so
+// the backward pass carries psi back with the costate: K backward steps are
+// one fused launch at -theta over both states (fused.cu, mode 5), which adds
+// conj(lt_s) m_s at every phase point; G's double-float planes are read and
+// written once per launch, and nothing is recomputed or stored per step.
 //
-// Checkpointing: the forward keeps psi every `ckpt` steps; the backward walks
-// the segments from the last, recomputes each segment's mid-step states from
-// its checkpoint (fused.cu, mode 1) and then steps the costate back through it.
+// Checkpointing: the forward keeps psi at the end of every segment of `ckpt`
+// steps; the backward walks the segments from the last, restarting psi from
+// the segment's checkpoint, so that the FP32 rounding of psi stepped
+// backward accumulates over at most one segment.
+//
+// Bytes per site and step (FP32, K steps per launch): 72/K for the backward
+// launches (psi and lambda read and written, 32; the table, 8; G read and
+// written, 32), plus 16 per segment for the checkpoint.  The forward pass is
+// ts_evolve plus one checkpoint copy (16 B) per segment.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -26,6 +36,10 @@
 #include "internal.h"
 #include "trace.h"
 
+#ifndef TS_ADJ_DEFAULT_K      // fused depth of the recomputation and backward launches
+#define TS_ADJ_DEFAULT_K 2
+#endif
+
 namespace {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -33,16 +47,14 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Workspace planes, each of the grid's plane size.
 enum : int {
     WS_T = 0,      // target phi: re, im
-    WS_LA = 2,     // costate ping-pong pair A: re, im
-    WS_LB = 4,     // ... pair B
-    WS_RA = 6,     // recomputation ping-pong pair A
-    WS_RB = 8,     // ... pair B
+    WS_QA = 2,     // backward ping-pong quad A: psi re, im, lambda re, im
+    WS_QB = 6,     // ... quad B
     WS_G = 10,     // G as double-float: re hi, re lo, im hi, im lo
-    WS_CK = 14     // checkpoints (2 planes each), then the mid-step states
+    WS_CK = 14     // checkpoints, 2 planes each
 };
 
 struct WsLayout {
-    int64_t n_ck;          // checkpoints: psi at steps 0, ckpt, 2 ckpt, ...
+    int64_t n_ck;          // checkpoints: psi at steps ckpt, 2 ckpt, ..., steps
     int64_t n_planes;
     size_t scratch_off;    // partials and result of the overlap reduction
     size_t bytes;
@@ -53,7 +65,7 @@ WsLayout ws_layout(const ts_grid *g, int64_t steps, int64_t ckpt)
     WsLayout w;
     w.n_ck = (steps + ckpt - 1) / ckpt;
     if (w.n_ck < 1) w.n_ck = 1;
-    w.n_planes = WS_CK + 2 * w.n_ck + 2 * ckpt;
+    w.n_planes = WS_CK + 2 * w.n_ck;
     w.scratch_off = (size_t)w.n_planes * g->L.plane_bytes;
     w.bytes = w.scratch_off + round_up(sizeof(double) * ts::OBS_MAX_BLOCKS * ts::OBS_Q, 256) +
               round_up(sizeof(double) * ts::OBS_Q, 256);
@@ -151,8 +163,8 @@ ts_status ts_adjoint_forward(ts_grid *g, const void *target_re, const void *targ
         const void *s = src[c];
         if (where == TS_HOST) {
             const size_t nbytes = (size_t)nx * ny * (f64 ? 8 : 4);
-            e = cudaMemcpyAsync(plane(WS_LA), s, nbytes, cudaMemcpyHostToDevice, st);
-            s = plane(WS_LA);
+            e = cudaMemcpyAsync(plane(WS_QA), s, nbytes, cudaMemcpyHostToDevice, st);
+            s = plane(WS_QA);
         }
         if (e == cudaSuccess)
             e = ts::launch_convert_in(s, f64, plane(WS_T + c), false, nx, ny, pitch, st);
@@ -160,13 +172,14 @@ ts_status ts_adjoint_forward(ts_grid *g, const void *target_re, const void *targ
     }
     if (e != cudaSuccess) return cuda_err(e, "ts_adjoint_forward: target");
 
-    // forward with checkpoints (psi at steps 0, ckpt, 2 ckpt, ...)
+    // forward with checkpoints (psi at the end of each segment: steps ckpt,
+    // 2 ckpt, ..., steps)
     for (int64_t k = 0; k < w.n_ck; ++k) {
-        e = cudaMemcpyAsync(plane(WS_CK + 2 * k), g->re(), 2 * PB, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return cuda_err(e, "ts_adjoint_forward: checkpoint");
         const int64_t n = std::min(ckpt_every, steps - k * ckpt_every);
         ts_status s = ts_evolve(g, n, 0, stream);
         if (s != TS_OK) return s;
+        e = cudaMemcpyAsync(plane(WS_CK + 2 * k), g->re(), 2 * PB, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_err(e, "ts_adjoint_forward: checkpoint");
     }
 
     // c = <phi|psi_T>
@@ -202,10 +215,15 @@ ts_status ts_adjoint_forward(ts_grid *g, const void *target_re, const void *targ
     return TS_OK;
 }
 
-ts_status ts_adjoint_backward(ts_grid *g, void *ws, size_t ws_bytes, float *grad, void *stream)
+ts_status ts_adjoint_backward_depth(ts_grid *g, void *ws, size_t ws_bytes, int K, float *grad,
+                                    void *stream)
 {
     ts::TraceRange trace_("ts_adjoint_backward");
     if (!g || !ws || !grad) return err(TS_ERR_ARG, "ts_adjoint_backward: null argument");
+    if (K < 0 || K > ts::FUSED_ADJ_MAX_K)
+        return err(TS_ERR_ARG, "ts_adjoint_backward: depth K must be in [0, %d]",
+                   ts::FUSED_ADJ_MAX_K);
+    const int KA = K > 0 ? K : TS_ADJ_DEFAULT_K;
     AdjointState a;
     {
         std::lock_guard<std::mutex> lk(g_adj_mu);
@@ -223,30 +241,28 @@ ts_status ts_adjoint_backward(ts_grid *g, void *ws, size_t ws_bytes, float *grad
     const int nx = (int)g->L.nx, ny = (int)g->L.ny;
     const int64_t pitch = g->L.pitch;
 
-    CUtensorMap tmL[2], tmR[2];
+    // the two quads (psi, lambda) and, for the backward launches' L2
+    // prefetches, the four G planes
+    CUtensorMap tmQ[2], tmG;
     const char *why = "";
-    if (!ts::make_pair_tensor_map(&tmL[0], plane(WS_LA), nx, ny, pitch, PB, &why) ||
-        !ts::make_pair_tensor_map(&tmL[1], plane(WS_LB), nx, ny, pitch, PB, &why) ||
-        !ts::make_pair_tensor_map(&tmR[0], plane(WS_RA), nx, ny, pitch, PB, &why) ||
-        !ts::make_pair_tensor_map(&tmR[1], plane(WS_RB), nx, ny, pitch, PB, &why))
+    if (!ts::make_pair_tensor_map(&tmQ[0], plane(WS_QA), nx, ny, pitch, PB, &why, 4) ||
+        !ts::make_pair_tensor_map(&tmQ[1], plane(WS_QB), nx, ny, pitch, PB, &why, 4) ||
+        !ts::make_pair_tensor_map(&tmG, plane(WS_G), nx, ny, pitch, PB, &why, 4))
         return err(TS_ERR_CUDA, "ts_adjoint_backward: %s", why);
 
-    cudaError_t e = cudaMemcpyAsync(plane(WS_LA), plane(WS_T), 2 * PB, cudaMemcpyDeviceToDevice, st);
+    // lambda_T = phi (in quad A), G = 0
+    cudaError_t e =
+        cudaMemcpyAsync(plane(WS_QA + 2), plane(WS_T), 2 * PB, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(plane(WS_G), 0, 4 * PB, st);
     if (e != cudaSuccess) return cuda_err(e, "ts_adjoint_backward: set-up");
 
-    ts::FusedLaunch fw;
-    fw.tm_phase = &g->tm_phase;
-    fw.nx = nx;
-    fw.ny = ny;
-    fw.pitch = pitch;
-    fw.err = g->err;
-    ts::FusedLaunch bw = fw;
-    fw.t1 = (float)g->t1;   // forward recomputation at +theta
-    fw.s1 = (float)g->s1;
-    fw.g1 = (float)g->g1;
-    fw.t2 = (float)g->t2;
-    fw.s2 = (float)g->s2;
+    ts::FusedLaunch bw;
+    bw.tm_phase = &g->tm_phase;
+    bw.tm_x = &tmG;
+    bw.nx = nx;
+    bw.ny = ny;
+    bw.pitch = pitch;
+    bw.err = g->err;
     bw.t1 = -(float)g->t1;  // backward steps U^dagger at -theta
     bw.s1 = -(float)g->s1;
     bw.g1 = (float)g->g1;
@@ -257,32 +273,25 @@ ts_status ts_adjoint_backward(ts_grid *g, void *ws, size_t ws_bytes, float *grad
     bw.g_ih = (float *)plane(WS_G + 2);
     bw.g_il = (float *)plane(WS_G + 3);
 
-    int lc = 0;   // costate in pair lc (0: LA, 1: LB)
-    const int64_t mid0 = WS_CK + 2 * w.n_ck;
+    int q = 0;   // psi and lambda in quad q (0: QA, 1: QB)
+    auto quad = [&](int i) { return i ? WS_QB : WS_QA; };
     for (int64_t k = w.n_ck - 1; k >= 0; --k) {
         const int64_t n = std::min(a.ckpt, a.steps - k * a.ckpt);
-        e = cudaMemcpyAsync(plane(WS_RA), plane(WS_CK + 2 * k), 2 * PB, cudaMemcpyDeviceToDevice, st);
+        // psi at the end of segment k, beside the costate
+        e = cudaMemcpyAsync(plane(quad(q)), plane(WS_CK + 2 * k), 2 * PB, cudaMemcpyDeviceToDevice,
+                            st);
         if (e != cudaSuccess) return cuda_err(e, "ts_adjoint_backward: restore checkpoint");
-        int rc = 0;
-        for (int64_t i = 0; i < n; ++i) {        // recompute m_s for the segment
-            fw.tm_state = &tmR[rc];
-            fw.out_re = (float *)plane(rc ? WS_RA : WS_RB);
-            fw.out_im = (float *)plane((rc ? WS_RA : WS_RB) + 1);
-            fw.m_re = (float *)plane(mid0 + 2 * i);
-            fw.m_im = (float *)plane(mid0 + 2 * i + 1);
-            e = ts::launch_fused_mid(1, fw, st);
-            if (e != cudaSuccess) return cuda_err(e, "ts_adjoint_backward: recompute launch");
-            rc ^= 1;
-        }
-        for (int64_t i = n - 1; i >= 0; --i) {   // costate back through the segment
-            bw.tm_state = &tmL[lc];
-            bw.out_re = (float *)plane(lc ? WS_LA : WS_LB);
-            bw.out_im = (float *)plane((lc ? WS_LA : WS_LB) + 1);
-            bw.m_re = (float *)plane(mid0 + 2 * i);
-            bw.m_im = (float *)plane(mid0 + 2 * i + 1);
-            e = ts::launch_fused_mid(2, bw, st);
+        for (int64_t i = n; i > 0;) {            // steps i, i - 1, ..., i - kk + 1 of the segment
+            const int kk = (int)std::min<int64_t>(KA, i);
+            bw.tm_state = &tmQ[q];
+            bw.out_re = (float *)plane(quad(q ^ 1));
+            bw.out_im = (float *)plane(quad(q ^ 1) + 1);
+            bw.out2_re = (float *)plane(quad(q ^ 1) + 2);
+            bw.out2_im = (float *)plane(quad(q ^ 1) + 3);
+            e = ts::launch_fused_adjoint(kk, bw, st);
             if (e != cudaSuccess) return cuda_err(e, "ts_adjoint_backward: backward launch");
-            lc ^= 1;
+            q ^= 1;
+            i -= kk;
         }
     }
     const int64_t sites = (int64_t)nx * ny;
@@ -302,6 +311,11 @@ ts_status ts_adjoint_backward(ts_grid *g, void *ws, size_t ws_bytes, float *grad
         return err(TS_ERR_TIMEOUT, "ts_adjoint_backward: a bounded wait gave up (error word %d)", h);
     }
     return TS_OK;
+}
+
+ts_status ts_adjoint_backward(ts_grid *g, void *ws, size_t ws_bytes, float *grad, void *stream)
+{
+    return ts_adjoint_backward_depth(g, ws, ws_bytes, 0, grad, stream);
 }
 
 ts_status ts_adjoint_grad(ts_grid *g, const void *target_re, const void *target_im,

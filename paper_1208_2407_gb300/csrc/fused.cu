@@ -48,6 +48,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <queue>
+#include <type_traits>
 #include <utility>
 #include <vector>
 #include <cudaTypedefs.h>
@@ -112,6 +113,12 @@ namespace {
 #ifndef TS_FUSED_FFMA2           // packed FP32 FMAs (__ffma2_rn): see Cfg<K>::PACKED
 #define TS_FUSED_FFMA2 1
 #endif
+#ifndef TS_FUSED_ADJ_PF          // backward adjoint steps: row pairs of G prefetched into
+#define TS_FUSED_ADJ_PF 2        // L2 ahead of their plain loads (0: none)
+#endif
+#ifndef TS_FUSED_PF_DUAL         // row pairs prefetched ahead of use by the backward
+#define TS_FUSED_PF_DUAL 2       // adjoint steps (two states per slot)
+#endif
 constexpr int PLANE_SLOT_BYTES = FUSED_BOX_ROWS * FUSED_BOX_COLS * 4;   // 1 KiB
 constexpr int SLOT_BYTES = 2 * PLANE_SLOT_BYTES;     // one ring slot: two planes of 2 rows
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;    // 2 s per wait
@@ -129,11 +136,19 @@ constexpr uint32_t FULL = 0xffffffffu;
 // the phase ring and the b substep's in a third, shorter ring (the b ring):
 // only substep 2 reads it, at iterations j + 2 and j + 3 of row pair j.
 __host__ __device__ constexpr int phase_planes(int mode) { return mode == 3 ? 3 : 2; }
+// Planes of a state-ring slot: (re, im); the backward adjoint steps (MODE 5)
+// carry two states, the forward state psi and the costate lambda.
+__host__ __device__ constexpr int state_planes(int mode) { return mode == 5 ? 4 : 2; }
 
-// __launch_bounds__ minimum resident blocks of the single-grid kernel
-__host__ __device__ constexpr int min_blocks(int K)
+// __launch_bounds__ minimum resident blocks of the single-grid kernel; the
+// backward adjoint steps (MODE 5) carry two states and K - 1 running sums of
+// G's terms, and are not held to the forward depth's occupancy
+__host__ __device__ constexpr int min_blocks(int K, int MODE = 0)
 {
-    return K == 3 ? TS_FUSED_MIN_BLOCKS_K3 : K == 4 ? TS_FUSED_MIN_BLOCKS_K4 : TS_FUSED_MIN_BLOCKS;
+    return MODE == 5   ? TS_FUSED_MIN_BLOCKS
+           : K == 3    ? TS_FUSED_MIN_BLOCKS_K3
+           : K == 4    ? TS_FUSED_MIN_BLOCKS_K4
+                       : TS_FUSED_MIN_BLOCKS;
 }
 
 // ... and of the multi-grid kernel
@@ -144,10 +159,13 @@ __host__ __device__ constexpr int multi_min_blocks(int K)
                     : TS_FUSED_MIN_BLOCKS;
 }
 
-template <int K, int PP = 2, bool BRING = false>
+template <int K, int PP = 2, bool BRING = false, int SP = 2>
 struct Cfg {
     static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
-    static constexpr int PF = K == 1 ? TS_FUSED_PF_K1 : K == 2 ? TS_FUSED_PF_K2 : TS_FUSED_PF_DEEP;
+    static constexpr int PF = SP == 4 ? TS_FUSED_PF_DUAL
+                              : K == 1 ? TS_FUSED_PF_K1
+                              : K == 2 ? TS_FUSED_PF_K2
+                                       : TS_FUSED_PF_DEEP;
     static constexpr bool PINGPONG = K >= TS_FUSED_PINGPONG_MIN_K && K <= TS_FUSED_PINGPONG_MAX_K;
     // packed FP32 FMAs in the Y sweeps and the phase: 0 never, 1 for every
     // depth but 2 (where the scalar form measured faster), 2 always
@@ -162,13 +180,29 @@ struct Cfg {
     // waited for at r + 2, so the ring holds r in [j - 3, j - 2 + PF]
     static constexpr int NSB = BRING ? PF + 2 : 0;
     static constexpr int NBAR = NSS + NSP + NSB;   // mbarriers per warp
-    static constexpr int WARP_SMEM = NSS * SLOT_BYTES + NSP * PSLOT + NSB * SLOT_BYTES;
+    static constexpr int SSLOT = SP * PLANE_SLOT_BYTES;   // a state slot
+    static constexpr int WARP_SMEM = NSS * SSLOT + NSP * PSLOT + NSB * SLOT_BYTES;
     static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + NBAR * 8);
 };
 
+// The configuration of a mode's kernel at depth K.
+template <int K, int MODE>
+using CfgM = Cfg<K, phase_planes(MODE), MODE == 4, state_planes(MODE)>;
+
+// Four columns of one row of one state, held by one lane.
 struct Frag {
     float4 re, im;
 };
+
+// The same columns of two states that take the same factors: the forward
+// state psi (a) and the costate lambda (b) of a backward adjoint step.
+struct Frag2 {
+    Frag a, b;
+};
+
+// The per-lane state of a mode: one state, or two for the backward steps.
+template <int MODE>
+using StateT = std::conditional_t<MODE == 5, Frag2, Frag>;
 
 struct KParams {
     float *out_re, *out_im;
@@ -182,11 +216,13 @@ struct KParams {
                              // crosses a slab boundary (ny_slab even)
     float t1, s1, g1, t2, s2;
     int *err;
-    // adjoint support (K = 1 only): MODE 1 writes the mid-step state m (after
-    // the phase) to (m_re, m_im); MODE 2 reads it and accumulates
-    // G += conj(lt) m, with lt the state at the phase point, into the
-    // double-float planes (g_rh + g_rl, g_ih + g_il)
-    float *m_re, *m_im;
+    // MODE 5 (backward adjoint steps): the costate's output planes (out_re,
+    // out_im take psi), and G as double-float planes (g_rh + g_rl,
+    // g_ih + g_il).  At each step's phase point the lane's rows add
+    // conj(lambda~) m, lambda~ = B^dagger lambda_s and m = B^dagger psi_s the
+    // mid-step state; a row's K terms are summed in FP32 inside the launch
+    // and added into G once.
+    float *out2_re, *out2_im;
     float *g_rh, *g_rl, *g_ih, *g_il;
     // MODE 3 (time-dependent potential V0 + a(t) V1): a_n dt / 2 of step k
     // of the launch; the phase ring carries V1 as a third plane
@@ -216,6 +252,16 @@ __device__ __forceinline__ void tma_load_pair(void *dst, const CUtensorMap *tm, 
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
         "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(0), "r"(smem_addr(bar))
         : "memory");
+}
+
+// Bring one box (x in [x, x+128), rows y, y+1, planes from z) into L2 without
+// waiting for it: the plain loads that read those rows later hit in L2.
+__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap *tm, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
 }
 
 // ---- register-level sweeps ------------------------------------------------
@@ -326,6 +372,33 @@ __device__ __forceinline__ void phase4(Frag &f, float4 g, float4 s)
     }
 }
 
+// Both states of a backward adjoint step take the same factor.
+__device__ __forceinline__ void x_even(Frag2 &f, const XEven &c)
+{
+    x_even(f.a, c);
+    x_even(f.b, c);
+}
+
+__device__ __forceinline__ void x_odd(Frag2 &f, const XOdd &c)
+{
+    x_odd(f.a, c);
+    x_odd(f.b, c);
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void y_pair(Frag2 &a, Frag2 &b, float t, float s)
+{
+    y_pair<PACKED>(a.a, b.a, t, s);
+    y_pair<PACKED>(a.b, b.b, t, s);
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void phase4(Frag2 &f, float4 g, float4 s)
+{
+    phase4<PACKED>(f.a, g, s);
+    phase4<PACKED>(f.b, g, s);
+}
+
 // Drive phase exp(-i a dt V1) of one row of the lane (time-dependent
 // potential): adt = a_n dt of the step, v1 = the row's V1 values.
 // versine_short on two columns at once (same operations, same rounding)
@@ -383,6 +456,15 @@ __device__ __forceinline__ Frag zero_frag()
     return f;
 }
 
+template <typename S>
+__device__ __forceinline__ S zero_state()
+{
+    if constexpr (std::is_same_v<S, Frag2>)
+        return Frag2{zero_frag(), zero_frag()};
+    else
+        return zero_frag();
+}
+
 // Slot layout: [plane][row][128 floats]; state slots hold (re, im), phase
 // slots hold (gamma_V, s_V).
 __device__ __forceinline__ float4 lds4(const unsigned char *slot, int plane, int row, int lane)
@@ -411,15 +493,36 @@ __device__ __forceinline__ bool owns_row(const Owned &w, const KParams &p, int r
     return w.lane_ok && row >= w.Y0 && row < w.Y1 && row < p.ny;
 }
 
-// Adjoint hook at the phase point of a backward step: G += conj(lt) m for one
-// owned row (lt = this row of the costate after B^dagger, m = the forward
-// mid-step state of the same step).
-__device__ __forceinline__ void mid_accumulate(const Frag &lt, int row, const Owned &w,
-                                               const KParams &p)
+// Adjoint hooks.  At the phase point of a backward step the lane's rows of
+// the costate, lt = B^dagger lambda_s, meet the mid-step state of the same
+// step, m = B^dagger psi_s: the term conj(lt) m = (lr mr + li mi) + i (lr mi - li mr).
+__device__ __forceinline__ Frag adj_term(const Frag &lt, const Frag &m)
+{
+    Frag t;
+    t.re = make_float4(fmaf(lt.re.x, m.re.x, lt.im.x * m.im.x),
+                       fmaf(lt.re.y, m.re.y, lt.im.y * m.im.y),
+                       fmaf(lt.re.z, m.re.z, lt.im.z * m.im.z),
+                       fmaf(lt.re.w, m.re.w, lt.im.w * m.im.w));
+    t.im = make_float4(fmaf(lt.re.x, m.im.x, -lt.im.x * m.re.x),
+                       fmaf(lt.re.y, m.im.y, -lt.im.y * m.re.y),
+                       fmaf(lt.re.z, m.im.z, -lt.im.z * m.re.z),
+                       fmaf(lt.re.w, m.im.w, -lt.im.w * m.re.w));
+    return t;
+}
+
+__device__ __forceinline__ Frag frag_add(const Frag &a, const Frag &b)
+{
+    Frag r;
+    r.re = make_float4(a.re.x + b.re.x, a.re.y + b.re.y, a.re.z + b.re.z, a.re.w + b.re.w);
+    r.im = make_float4(a.im.x + b.im.x, a.im.y + b.im.y, a.im.z + b.im.z, a.im.w + b.im.w);
+    return r;
+}
+
+// G += t for one owned row, in double-float (hi + lo planes)
+__device__ __forceinline__ void adj_commit(const Frag &t, int row, const Owned &w,
+                                           const KParams &p)
 {
     const int64_t o = (int64_t)row * p.pitch + w.xg;
-    const float4 mr = *reinterpret_cast<const float4 *>(p.m_re + o);
-    const float4 mi = *reinterpret_cast<const float4 *>(p.m_im + o);
     float4 rh = *reinterpret_cast<const float4 *>(p.g_rh + o);
     float4 rl = *reinterpret_cast<const float4 *>(p.g_rl + o);
     float4 ih = *reinterpret_cast<const float4 *>(p.g_ih + o);
@@ -431,27 +534,46 @@ __device__ __forceinline__ void mid_accumulate(const Frag &lt, int row, const Ow
         hi = s.hi;
         lo = s.lo;
     };
-    // conj(l) m = (lr mr + li mi) + i (lr mi - li mr)
-    acc(rh.x, rl.x, fmaf(lt.re.x, mr.x, lt.im.x * mi.x));
-    acc(rh.y, rl.y, fmaf(lt.re.y, mr.y, lt.im.y * mi.y));
-    acc(rh.z, rl.z, fmaf(lt.re.z, mr.z, lt.im.z * mi.z));
-    acc(rh.w, rl.w, fmaf(lt.re.w, mr.w, lt.im.w * mi.w));
-    acc(ih.x, il.x, fmaf(lt.re.x, mi.x, -lt.im.x * mr.x));
-    acc(ih.y, il.y, fmaf(lt.re.y, mi.y, -lt.im.y * mr.y));
-    acc(ih.z, il.z, fmaf(lt.re.z, mi.z, -lt.im.z * mr.z));
-    acc(ih.w, il.w, fmaf(lt.re.w, mi.w, -lt.im.w * mr.w));
+    acc(rh.x, rl.x, t.re.x);
+    acc(rh.y, rl.y, t.re.y);
+    acc(rh.z, rl.z, t.re.z);
+    acc(rh.w, rl.w, t.re.w);
+    acc(ih.x, il.x, t.im.x);
+    acc(ih.y, il.y, t.im.y);
+    acc(ih.z, il.z, t.im.z);
+    acc(ih.w, il.w, t.im.w);
     *reinterpret_cast<float4 *>(p.g_rh + o) = rh;
     *reinterpret_cast<float4 *>(p.g_rl + o) = rl;
     *reinterpret_cast<float4 *>(p.g_ih + o) = ih;
     *reinterpret_cast<float4 *>(p.g_il + o) = il;
 }
 
-__device__ __forceinline__ void mid_store(const Frag &m, int row, const Owned &w,
-                                          const KParams &p)
+// MODE 5 at the phase point of step k of the launch, rows (y1, y1 + 1) held
+// in (P, Q) (psi in .a, lambda in .b).  The pair reached step k here one
+// iteration after it reached step k - 1, so its running sum is carried in
+// registers: acc[2k], acc[2k+1] hold, between iterations, the sum of the
+// pair that is at step k now; car passes the sum of step k - 1 from the
+// previous iteration to this step.  Step K - 1 adds the finished sum into G
+// (owned rows only; other rows' sums are never stored).
+template <int K>
+__device__ __forceinline__ void adj_step(int k, const Frag2 &P, const Frag2 &Q, int y1,
+                                         Frag (&acc)[2 * K], Frag &carP, Frag &carQ,
+                                         const Owned &w, const KParams &p)
 {
-    const int64_t o = (int64_t)row * p.pitch + w.xg;
-    *reinterpret_cast<float4 *>(p.m_re + o) = m.re;
-    *reinterpret_cast<float4 *>(p.m_im + o) = m.im;
+    Frag tP = adj_term(P.b, P.a), tQ = adj_term(Q.b, Q.a);
+    if (k > 0) {
+        tP = frag_add(carP, tP);
+        tQ = frag_add(carQ, tQ);
+    }
+    if (k == K - 1) {
+        if (owns_row(w, p, y1)) adj_commit(tP, y1, w, p);
+        if (owns_row(w, p, y1 + 1)) adj_commit(tQ, y1 + 1, w, p);
+    } else {
+        carP = acc[2 * k];
+        carQ = acc[2 * k + 1];
+        acc[2 * k] = tP;
+        acc[2 * k + 1] = tQ;
+    }
 }
 
 __device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
@@ -460,22 +582,23 @@ __device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y
 // `cin` and leave through `cout` (each slot is read before it is written, so
 // the two may be the same array).  INTERIOR: every Y pair and
 // every phase row the iteration touches lies on the grid and in the ring,
-// so no masks or range checks are needed.  MODE 0: a plain step; MODE 1
-// (K = 1): also store the mid-step state; MODE 2 (K = 1): a backward step
-// U^dagger (the caller passes the coefficients at -theta; the phase is
-// conjugated here) that accumulates G at its phase point.
-template <int K, bool INTERIOR, int MODE>
-__device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&cout)[2 * K],
-                                              Frag a, Frag b, int yin, int j,
+// so no masks or range checks are needed.  MODE 0: plain steps; MODE 3: a
+// time-dependent potential; MODE 4: one fourth-order step; MODE 5: backward
+// adjoint steps U^dagger on two states (the caller passes the coefficients at
+// -theta; the phase is conjugated here) that accumulate G at each step's
+// phase point, with the running sums of the rows in flight carried in `acc`
+// (updated in place).
+template <int K, bool INTERIOR, int MODE, typename S = StateT<MODE>>
+__device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2 * K],
+                                              Frag (&acc)[2 * K], S a, S b, int yin, int j,
                                               const unsigned char *ring_p, int pos_p,
                                               const unsigned char *ring_b, int cnt_b,
                                               const StripCoef &c, const KParams &p, int lane,
-                                              const Owned &w, Frag &O0, Frag &O1)
+                                              const Owned &w, S &O0, S &O1)
 {
-    static_assert(MODE == 0 || MODE == 3 || MODE == 4 || K == 1,
-                  "mid-step modes exist for K = 1 only");
     static_assert(MODE != 4 || K == 5, "the fused fourth-order step has five substeps");
-    using C = Cfg<K, phase_planes(MODE), MODE == 4>;
+    using C = CfgM<K, MODE>;
+    constexpr bool CONJ = MODE == 5;   // backward steps: exp(+i V dt), sine -s_V
     // MODE 4: substep k of U4 = a a b a a is b for k == 2 (angle and table)
     auto is_b = [](int k) { return MODE == 4 && k == 2; };
     constexpr int NSP = C::NSP;
@@ -500,34 +623,28 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
         const bool v = yok(yin);
         y_pair<C::PACKED>(a, b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
-    Frag P = cin[0], Q = a;       // rows (yin-1, yin)
+    S P = cin[0], Q = a;          // rows (yin-1, yin)
     {
         const bool v = yok(yin - 1);
         y_pair<C::PACKED>(P, Q, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
     }
     cout[0] = b;
     int y1 = yin - 1;
-    if constexpr (MODE == 2) {
-        if (owns_row(w, p, y1)) mid_accumulate(P, y1, w, p);
-        if (owns_row(w, p, y1 + 1)) mid_accumulate(Q, y1 + 1, w, p);
-    }
+    Frag carP, carQ;   // MODE 5: running sums handed from step k - 1 to step k
+    if constexpr (MODE == 5) adj_step<K>(0, P, Q, y1, acc, carP, carQ, w, p);
     // phase of step 0 on rows (y1, y1+1): slot j-1 row 1, slot j row 0
     // (conjugated in a backward step: exp(+i V dt) has sine -s_V)
     if (INTERIOR || j >= 1) {
         const unsigned char *sp = slot_p(1);
         const float4 sv = lds4(sp, 1, 1, lane);
-        phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), MODE == 2 ? neg4(sv) : sv);
+        phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), CONJ ? neg4(sv) : sv);
         if constexpr (MODE == 3) drive4<C::PACKED>(P, lds4(sp, 2, 1, lane), p.adt[0]);
     }
     {
         const unsigned char *sp = slot_p(0);
         const float4 sv = lds4(sp, 1, 0, lane);
-        phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), MODE == 2 ? neg4(sv) : sv);
+        phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), CONJ ? neg4(sv) : sv);
         if constexpr (MODE == 3) drive4<C::PACKED>(Q, lds4(sp, 2, 0, lane), p.adt[0]);
-    }
-    if constexpr (MODE == 1) {
-        if (owns_row(w, p, y1)) mid_store(P, y1, w, p);
-        if (owns_row(w, p, y1 + 1)) mid_store(Q, y1 + 1, w, p);
     }
 #pragma unroll
     for (int k = 1; k < K; ++k) {
@@ -550,7 +667,7 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
         x_even(Q, Em);
         x_odd(P, Ok);
         x_odd(Q, Ok);
-        Frag P2 = cin[2 * k - 1], Q2 = P;     // rows (y1-1, y1)
+        S P2 = cin[2 * k - 1], Q2 = P;        // rows (y1-1, y1)
         {   // Ye (merged), shifted: pair (y1-1, y1)
             const bool v = yok(y1 - 1);
             y_pair<C::PACKED>(P2, Q2, v ? tm : 0.f, v ? sm : 0.f);
@@ -564,17 +681,21 @@ __device__ __forceinline__ void pipeline_step(const Frag (&cin)[2 * K], Frag (&c
         cout[2 * k] = Q2;
         Q = P2;
         y1 -= 2;
+        if constexpr (MODE == 5) adj_step<K>(k, P, Q, y1, acc, carP, carQ, w, p);
         // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
-        // (MODE 4: the b substep's table comes from the b ring)
+        // (MODE 4: the b substep's table comes from the b ring; MODE 5: the
+        // conjugate phase, sine -s_V)
         auto slot_k = [&](int back) { return bk ? slot_b(back) : slot_p(back); };
         if (INTERIOR || j - k - 1 >= 0) {
             const unsigned char *sp = slot_k(k + 1);
-            phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), lds4(sp, 1, 1, lane));
+            const float4 sv = lds4(sp, 1, 1, lane);
+            phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), CONJ ? neg4(sv) : sv);
             if constexpr (MODE == 3) drive4<C::PACKED>(P, lds4(sp, 2, 1, lane), p.adt[k]);
         }
         if (INTERIOR || j - k >= 0) {
             const unsigned char *sp = slot_k(k);
-            phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), lds4(sp, 1, 0, lane));
+            const float4 sv = lds4(sp, 1, 0, lane);
+            phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), CONJ ? neg4(sv) : sv);
             if constexpr (MODE == 3) drive4<C::PACKED>(Q, lds4(sp, 2, 0, lane), p.adt[k]);
         }
     }
@@ -610,10 +731,10 @@ struct WarpRings {
     int cnt_b;
 };
 
-template <int K, int PP = 2, bool BRING = false>
+template <int K, int PP = 2, bool BRING = false, int SP = 2>
 __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int warp, int lane)
 {
-    using C = Cfg<K, PP, BRING>;
+    using C = Cfg<K, PP, BRING, SP>;
     constexpr int NSS = C::NSS, NSP = C::NSP, NBAR = C::NBAR;
     WarpRings r;
     // barriers first, then 1 KiB-aligned slots (state ring, phase ring, b ring)
@@ -624,7 +745,7 @@ __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int wa
     const uint32_t slots_off =
         ((base_addr + C::WPC * NBAR * 8 + 1023u) & ~1023u) - base_addr;
     r.ring_s = smem_raw + slots_off + (size_t)warp * C::WARP_SMEM;
-    r.ring_p = r.ring_s + NSS * SLOT_BYTES;
+    r.ring_p = r.ring_s + NSS * C::SSLOT;
     r.ring_b = r.ring_p + NSP * C::PSLOT;
     r.pos_s = r.pos_p = 0;
     r.par_s = r.par_p = 0;
@@ -643,18 +764,18 @@ __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int wa
 // outstanding copies are drained).
 // Per-segment constants of one warp.
 struct Seg {
-    const CUtensorMap *tm_state, *tm_phase, *tm_b;
+    const CUtensorMap *tm_state, *tm_phase, *tm_b, *tm_x;   // MODE 5: tm_x the G planes
     int XL, xg, Y0, Y1, Ys, n_iter, lane;
     bool store_lane;
     StripCoef c;
     Owned own;
 };
 
-template <int K>
+template <int SSLOT>
 __device__ __forceinline__ void issue_state(WarpRings &r, const Seg &s, int pos, int j)
 {
-    mbar_expect_tx(&r.bar_s[pos], SLOT_BYTES);
-    tma_load_pair(r.ring_s + pos * SLOT_BYTES, s.tm_state, s.XL, s.Ys + 2 * j, &r.bar_s[pos]);
+    mbar_expect_tx(&r.bar_s[pos], SSLOT);
+    tma_load_pair(r.ring_s + pos * SSLOT, s.tm_state, s.XL, s.Ys + 2 * j, &r.bar_s[pos]);
 }
 
 // b ring (MODE 4): the b substep's (gamma, s) rows of row pair j, copy
@@ -690,12 +811,12 @@ struct Issued {
     int s, p, b;
 };
 
-template <int K, int MODE, bool INTERIOR>
+template <int K, int MODE, bool INTERIOR, typename S = StateT<MODE>>
 __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KParams &p, int j,
-                                         const Frag (&cin)[2 * K], Frag (&cout)[2 * K],
-                                         Issued &iss)
+                                         const S (&cin)[2 * K], S (&cout)[2 * K],
+                                         Frag (&acc)[2 * K], Issued &iss)
 {
-    using C = Cfg<K, phase_planes(MODE), MODE == 4>;
+    using C = CfgM<K, MODE>;
     constexpr int NSS = C::NSS, NSP = C::NSP, NSB = C::NSB;
     const int lane = s.lane;
     bool ok = mbar_wait(&r.bar_s[r.pos_s], r.par_s, WAIT_LIMIT_NS) &&
@@ -719,27 +840,45 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
         }
         return false;
     }
-    const unsigned char *sj = r.ring_s + r.pos_s * SLOT_BYTES;
-    Frag a, b;
-    a.re = lds4(sj, 0, 0, lane);
-    a.im = lds4(sj, 1, 0, lane);
-    b.re = lds4(sj, 0, 1, lane);
-    b.im = lds4(sj, 1, 1, lane);
+    const unsigned char *sj = r.ring_s + r.pos_s * C::SSLOT;
+    // rows 0 and 1 of a state slot's planes (re, im) -- and (re, im) of the
+    // costate in planes 2 and 3 for the backward adjoint steps
+    auto load_rows = [&](Frag &a, Frag &b, int plane0) {
+        a.re = lds4(sj, plane0, 0, lane);
+        a.im = lds4(sj, plane0 + 1, 0, lane);
+        b.re = lds4(sj, plane0, 1, lane);
+        b.im = lds4(sj, plane0 + 1, 1, lane);
+    };
+    auto store_rows = [&](const Frag &o0, const Frag &o1, float *out_re, float *out_im, int yo) {
+        float *rr = out_re + (int64_t)yo * p.pitch + s.xg;
+        float *mm = out_im + (int64_t)yo * p.pitch + s.xg;
+        if (INTERIOR || yo < p.ny) {
+            *reinterpret_cast<float4 *>(rr) = o0.re;
+            *reinterpret_cast<float4 *>(mm) = o0.im;
+        }
+        if (INTERIOR || yo + 1 < p.ny) {
+            *reinterpret_cast<float4 *>(rr + p.pitch) = o1.re;
+            *reinterpret_cast<float4 *>(mm + p.pitch) = o1.im;
+        }
+    };
+    S a, b;
+    if constexpr (MODE == 5) {
+        load_rows(a.a, b.a, 0);
+        load_rows(a.b, b.b, 2);
+    } else {
+        load_rows(a, b, 0);
+    }
     const int yin = s.Ys + 2 * j;
-    Frag O0, O1;
-    pipeline_step<K, INTERIOR, MODE>(cin, cout, a, b, yin, j, r.ring_p, r.pos_p, r.ring_b,
+    S O0, O1;
+    pipeline_step<K, INTERIOR, MODE>(cin, cout, acc, a, b, yin, j, r.ring_p, r.pos_p, r.ring_b,
                                      r.cnt_b, s.c, p, lane, s.own, O0, O1);
     const int yo = yin - 2 * K;
     if (s.store_lane && yo >= s.Y0 && yo < s.Y1) {
-        float *rr = p.out_re + (int64_t)yo * p.pitch + s.xg;
-        float *mm = p.out_im + (int64_t)yo * p.pitch + s.xg;
-        if (INTERIOR || yo < p.ny) {
-            *reinterpret_cast<float4 *>(rr) = O0.re;
-            *reinterpret_cast<float4 *>(mm) = O0.im;
-        }
-        if (INTERIOR || yo + 1 < p.ny) {
-            *reinterpret_cast<float4 *>(rr + p.pitch) = O1.re;
-            *reinterpret_cast<float4 *>(mm + p.pitch) = O1.im;
+        if constexpr (MODE == 5) {
+            store_rows(O0.a, O1.a, p.out_re, p.out_im, yo);
+            store_rows(O0.b, O1.b, p.out2_re, p.out2_im, yo);
+        } else {
+            store_rows(O0, O1, p.out_re, p.out_im, yo);
         }
     }
     // state slot j and phase slot j-K are no longer read: refill them with
@@ -751,12 +890,19 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     const bool more_b = MODE == 4 && j >= 3 && jb < s.n_iter;
     if (lane == 0 && (more_s || more_p || more_b)) {
         fence_proxy_async();
-        if (more_s) issue_state<K>(r, s, r.pos_s, js);
+        if (more_s) issue_state<C::SSLOT>(r, s, r.pos_s, js);
         if (more_p)
             issue_phase<K, phase_planes(MODE)>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
         if constexpr (MODE == 4) {
             if (more_b) issue_b<NSB>(r, s, jb);   // the slot row pair j - 3 leaves
         }
+    }
+    if constexpr (MODE == 5 && TS_FUSED_ADJ_PF > 0) {
+        // into L2 ahead of their plain loads: the G rows that the last step
+        // adds into TS_FUSED_ADJ_PF iterations from now (row pair j + PF - K + 1)
+        const int q = j + TS_FUSED_ADJ_PF - K + 1, y = s.Ys + 2 * q;
+        if (lane == 0 && q >= 0 && q < s.n_iter && y >= 0 && y < p.ny)
+            tma_prefetch_l2(s.tm_x, s.XL, y, 0);
     }
     iss.s += more_s;
     iss.p += more_p;
@@ -772,15 +918,18 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
 template <int K, int MODE>
 __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_state,
                                             const CUtensorMap *tm_phase, const CUtensorMap *tm_b,
-                                            const KParams &p, int sx, int q0, int q1, int lane)
+                                            const CUtensorMap *tm_x, const KParams &p, int sx,
+                                            int q0, int q1, int lane)
 {
-    using C = Cfg<K, phase_planes(MODE), MODE == 4>;
+    using C = CfgM<K, MODE>;
+    using S = StateT<MODE>;
     constexpr int NSS = C::NSS, NSP = C::NSP, NSB = C::NSB, HALO = C::HALO, VALID = C::VALID;
     static_assert(NSB <= NSP, "the prologue issues the b ring inside the phase ring's loop");
     Seg s;
     s.tm_state = tm_state;
     s.tm_phase = tm_phase;
     s.tm_b = tm_b;
+    s.tm_x = tm_x;
     s.lane = lane;
     s.XL = sx * VALID - HALO;            // first loaded column (multiple of 4)
     s.xg = s.XL + 4 * lane;              // this lane's first column
@@ -812,7 +961,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     if (lane == 0) {
         fence_proxy_async();
         for (int j = 0; j < n_pro_p; ++j) {
-            if (j < n_pro_s) issue_state<K>(r, s, (r.pos_s + j) % NSS, j);
+            if (j < n_pro_s) issue_state<C::SSLOT>(r, s, (r.pos_s + j) % NSS, j);
             issue_phase<K, phase_planes(MODE)>(r, s, (r.pos_p + j) % NSP, j);
             if constexpr (MODE == 4) {
                 if (j < n_pro_b) issue_b<NSB>(r, s, j);
@@ -825,9 +974,16 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     // first reads set A and writes set B and the second goes back into A, so
     // no row is copied between iterations (at the price of registers, which
     // shallow pipelines keep for occupancy); edge row pairs update A in place.
-    Frag cA[2 * K], cB[2 * K];
+    // MODE 5: running sums of G's terms for the row pairs in flight (the
+    // sums of rows this warp owns start inside the segment; the rows of its
+    // first iterations are not this warp's and are never stored)
+    S cA[2 * K], cB[2 * K];
+    Frag acc[2 * K];
 #pragma unroll
-    for (int i = 0; i < 2 * K; ++i) cA[i] = zero_frag();
+    for (int i = 0; i < 2 * K; ++i) {
+        cA[i] = zero_state<S>();
+        acc[i] = zero_frag();
+    }
     auto interior = [&](int j) {
         const int yin = s.Ys + 2 * j;
         return j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny &&
@@ -836,17 +992,17 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     for (int j = 0; j < s.n_iter;) {
         if (j + 1 < s.n_iter && interior(j) && interior(j + 1)) {
             if (C::PINGPONG) {
-                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cB, iss)) return false;
-                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cB, cA, iss))
+                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cB, acc, iss)) return false;
+                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cB, cA, acc, iss))
                     return false;
             } else {
-                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cA, iss)) return false;
-                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cA, cA, iss))
+                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cA, acc, iss)) return false;
+                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cA, cA, acc, iss))
                     return false;
             }
             j += 2;
         } else {
-            if (!row_pair<K, MODE, false>(r, s, p, j, cA, cA, iss)) return false;
+            if (!row_pair<K, MODE, false>(r, s, p, j, cA, cA, acc, iss)) return false;
             j += 1;
         }
     }
@@ -869,16 +1025,17 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
 // One grid; the (strip, row-pair) units are split into equal contiguous
 // ranges, one per warp of a persistent launch.
 template <int K, int MODE>
-__global__ void __launch_bounds__(Cfg<K>::WPC * 32, min_blocks(K))
+__global__ void __launch_bounds__(Cfg<K>::WPC * 32, min_blocks(K, MODE))
 fused_kernel(const __grid_constant__ CUtensorMap tm_state,
              const __grid_constant__ CUtensorMap tm_phase,
-             const __grid_constant__ CUtensorMap tm_b, const KParams p)
+             const __grid_constant__ CUtensorMap tm_b,
+             const __grid_constant__ CUtensorMap tm_x, const KParams p)
 {
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * Cfg<K>::WPC + warp;
     if (gw >= p.total_warps) return;
-    WarpRings r = carve_rings<K, phase_planes(MODE), MODE == 4>(smem_raw, warp, lane);
+    WarpRings r = carve_rings<K, phase_planes(MODE), MODE == 4, state_planes(MODE)>(smem_raw, warp, lane);
     if (p.strip_warps > 0) {
         // strip-aligned split: warp (sx, i) takes row range i of strip sx, so
         // warps of neighbouring strips walk the same rows at the same time and
@@ -886,7 +1043,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
         const int sx = gw / p.strip_warps, i = gw - sx * p.strip_warps;
         const int q0 = (int)((int64_t)i * p.n_pairs / p.strip_warps);
         const int q1 = (int)((int64_t)(i + 1) * p.n_pairs / p.strip_warps);
-        if (q1 > q0) run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, p, sx, q0, q1, lane);
+        if (q1 > q0) run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, &tm_x, p, sx, q0, q1, lane);
         return;
     }
     const int64_t u_begin = (int64_t)gw * p.units / p.total_warps;
@@ -897,7 +1054,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
         const int64_t q1_want = (int64_t)q0 + (u_end - u);
         const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
         u += q1 - q0;
-        if (!run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, p, sx, q0, q1, lane)) return;
+        if (!run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, &tm_x, p, sx, q0, q1, lane)) return;
     }
 }
 
@@ -966,7 +1123,7 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
         const int q0 = (int)((int64_t)i * p.n_pairs / w);
         const int q1 = (int)((int64_t)(i + 1) * p.n_pairs / w);
         if (q1 > q0)
-            run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, p, sx, q0, q1, lane);
+            run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, nullptr, p, sx, q0, q1, lane);
         return;
     }
     const int64_t u_begin = (int64_t)gw * total_units / total_warps;
@@ -996,7 +1153,7 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
         if (q1_want > q0 + left_in_grid) q1_want = q0 + left_in_grid;
         const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
         u += q1 - q0;
-        if (!run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, p, sx, q0, q1, lane)) return;
+        if (!run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, nullptr, p, sx, q0, q1, lane)) return;
     }
 }
 
@@ -1038,7 +1195,7 @@ Occupancy occupancy_of(F kernel, int threads, int smem)
 template <int K, int MODE>
 cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
 {
-    using C = Cfg<K, phase_planes(MODE), MODE == 4>;
+    using C = CfgM<K, MODE>;
     static const Occupancy occ = occupancy_of(fused_kernel<K, MODE>, C::WPC * 32, C::SMEM);
     if (occ.err != cudaSuccess) return occ.err;
     const int blocks_per_sm = occ.blocks_per_sm, num_sms = occ.num_sms;
@@ -1072,8 +1229,8 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.t2 = a.t2;
     p.s2 = a.s2;
     p.err = a.err;
-    p.m_re = a.m_re;
-    p.m_im = a.m_im;
+    p.out2_re = a.out2_re;
+    p.out2_im = a.out2_im;
     p.g_rh = a.g_rh;
     p.g_rl = a.g_rl;
     p.g_ih = a.g_ih;
@@ -1086,7 +1243,8 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.sab = a.sab;
     const int blocks = (p.total_warps + C::WPC - 1) / C::WPC;
     fused_kernel<K, MODE><<<blocks, C::WPC * 32, C::SMEM, st>>>(
-        *a.tm_state, *a.tm_phase, a.tm_b ? *a.tm_b : *a.tm_phase, p);
+        *a.tm_state, *a.tm_phase, a.tm_b ? *a.tm_b : *a.tm_phase,
+        a.tm_x ? *a.tm_x : *a.tm_phase, p);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1254,15 +1412,19 @@ cudaError_t launch_fused_drive(int K, const FusedLaunch &a, cudaStream_t st)
 
 cudaError_t launch_fused_u4(const FusedLaunch &a, cudaStream_t st) { return launch_k<5, 4>(a, st); }
 
-cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st)
+cudaError_t launch_fused_adjoint(int K, const FusedLaunch &a, cudaStream_t st)
 {
-    if (mode == 1) return launch_k<1, 1>(a, st);
-    if (mode == 2) return launch_k<1, 2>(a, st);
-    return cudaErrorInvalidValue;
+    switch (K) {
+    case 1: return launch_k<1, 5>(a, st);
+    case 2: return launch_k<2, 5>(a, st);
+    case 3: return launch_k<3, 5>(a, st);
+    case 4: return launch_k<4, 5>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
-                          size_t plane_bytes, const char **why, int planes)
+                          size_t plane_bytes, const char **why, int planes, int box_planes)
 {
     // looked up once (thread-safe static initialisation)
     static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() {
@@ -1278,13 +1440,14 @@ bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int
         *why = "cuTensorMapEncodeTiled is not available from the driver";
         return false;
     }
-    if (planes < 1 || planes > 4) {
-        *why = "tensor map: 1 to 4 planes";
+    if (box_planes == 0) box_planes = planes;
+    if (box_planes < 1 || box_planes > 4 || planes < box_planes) {
+        *why = "tensor map: boxes of 1 to 4 planes, no more than the map has";
         return false;
     }
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)(pitch * 4), (cuuint64_t)plane_bytes};
-    cuuint32_t box[3] = {FUSED_BOX_COLS, FUSED_BOX_ROWS, (cuuint32_t)planes};
+    cuuint32_t box[3] = {FUSED_BOX_COLS, FUSED_BOX_ROWS, (cuuint32_t)box_planes};
     cuuint32_t estr[3] = {1, 1, 1};
     // (a driver call: the calling thread needs a current context)
     const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base),

@@ -98,6 +98,7 @@ struct FusedLaunch {
     const CUtensorMap *tm_state;   // (re, im) planes of the input pair, 3-D map
     const CUtensorMap *tm_phase;   // (gamma_V, s_V) planes, 3-D map
     const CUtensorMap *tm_b = nullptr;   // launch_fused_u4: the b substep's table
+    const CUtensorMap *tm_x = nullptr;   // launch_fused_adjoint: the 4 G planes
     float *out_re, *out_im;
     int nx, ny;
     int64_t pitch;
@@ -105,8 +106,9 @@ struct FusedLaunch {
     // versine form (g1 = 1 - cos theta, s1); at 2 theta: lifting (t2, s2)
     float t1, s1, g1, t2, s2;
     int *err;
-    // adjoint support (launch_fused_mid only)
-    float *m_re = nullptr, *m_im = nullptr;
+    // launch_fused_adjoint: the costate's output planes (out_re, out_im take
+    // psi) and G as double-float planes
+    float *out2_re = nullptr, *out2_im = nullptr;
     float *g_rh = nullptr, *g_rl = nullptr, *g_ih = nullptr, *g_il = nullptr;
     // time-dependent potential (launch_fused_drive only): a_n dt of step k
     float adt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -123,10 +125,14 @@ static_assert(sizeof(FusedLaunch::adt) / sizeof(float) == FUSED_MAX_K, "one a_n 
 constexpr int FUSED_BOX_COLS = 128;   // columns a warp strip loads (box width)
 constexpr int FUSED_BOX_ROWS = 2;     // rows per pipeline slot (box height)
 cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st);
-// One step (K = 1) with the adjoint hooks: mode 1 stores the mid-step state
-// in (m_re, m_im); mode 2 is a backward step (pass the coefficients at
-// -theta) that reads the mid-step state and accumulates G.
-cudaError_t launch_fused_mid(int mode, const FusedLaunch &a, cudaStream_t st);
+// K (1..FUSED_ADJ_MAX_K) backward adjoint steps U^dagger (pass the
+// coefficients at -theta) on two states at once: tm_state maps four planes
+// (psi re, im, lambda re, im), psi goes to (out_re, out_im) and lambda to
+// (out2_re, out2_im).  At each step's phase point G += conj(lambda~) m, with
+// lambda~ = B^dagger lambda_s and m = B^dagger psi_s; tm_x maps G's four
+// planes (for L2 prefetches of the rows about to be added into).
+constexpr int FUSED_ADJ_MAX_K = 4;
+cudaError_t launch_fused_adjoint(int K, const FusedLaunch &a, cudaStream_t st);
 // K (1..4) steps with the time-dependent potential V0 + a_n V1: tm_phase
 // maps three planes (gamma_V, s_V, V1) and adt[k] = a_n dt of step k.
 constexpr int FUSED_DRIVE_MAX_K = 4;
@@ -179,12 +185,14 @@ MultiPlan fused_multi_plan(int K, int n, const int *nx, const int *ny, EpochEntr
 cudaError_t launch_fused_multi(int K, const EpochEntry *tab, int n_grids, const MultiPlan &plan,
                                int flip, int *err, cudaStream_t st);
 
-// Build a 3-D FP32 tensor map over `planes` (2 to 4) consecutive pitched
-// planes (nx x ny each, `plane_bytes` apart) for the fused path: one box
-// load fetches the same rows of every plane.  Returns false (and a message)
-// if the driver entry point is unavailable or the encode call fails.
+// Build a 3-D FP32 tensor map over `planes` consecutive pitched planes
+// (nx x ny each, `plane_bytes` apart) for the fused path.  Its boxes span
+// 128 columns, 2 rows and `box_planes` planes (1 to 4; 0: all `planes`), so
+// one box load fetches the same rows of those planes.  Returns false (and a
+// message) if the driver entry point is unavailable or the encode call fails.
 bool make_pair_tensor_map(CUtensorMap *tm, const void *base, int nx, int ny, int64_t pitch,
-                          size_t plane_bytes, const char **why, int planes = 2);
+                          size_t plane_bytes, const char **why, int planes = 2,
+                          int box_planes = 0);
 
 // Thread-local count of kernel launches issued by this library.
 void count_launches(int64_t n);

@@ -105,6 +105,7 @@ _SIGNATURES = {
     "ts_adjoint_forward": [_VP, _VP, _VP, _INT, _INT, _I64, _I64, _VP, ctypes.c_size_t,
                            ctypes.POINTER(_DBL), ctypes.POINTER(_DBL), _VP],
     "ts_adjoint_backward": [_VP, _VP, ctypes.c_size_t, _VP, _VP],
+    "ts_adjoint_backward_depth": [_VP, _VP, ctypes.c_size_t, _INT, _VP, _VP],
     "ts_adjoint_grad": [_VP, _VP, _VP, _INT, _INT, _I64, _I64, _VP, ctypes.c_size_t, _VP,
                         ctypes.POINTER(_DBL), _VP],
     "ts_server_create": [ctypes.POINTER(ts_server_cfg), ctypes.POINTER(_VP)],
@@ -277,6 +278,10 @@ def ts_adjoint_forward(h, tre_ptr, tim_ptr, dtype, where, steps, ckpt_every, ws_
 
 def ts_adjoint_backward(h, ws_ptr, ws_bytes, grad_ptr, stream):
     _call("ts_adjoint_backward", h, ws_ptr, ws_bytes, grad_ptr, stream)
+
+
+def ts_adjoint_backward_depth(h, ws_ptr, ws_bytes, K, grad_ptr, stream):
+    _call("ts_adjoint_backward_depth", h, ws_ptr, ws_bytes, K, grad_ptr, stream)
 
 
 def ts_adjoint_grad(h, tre_ptr, tim_ptr, dtype, where, steps, ckpt_every, ws_ptr, ws_bytes,
@@ -476,9 +481,10 @@ class Grid:
 
 
 def adjoint_fidelity_grad(grid, target_re, target_im, steps: int, ckpt_every: int = 50,
-                          stream=None):
+                          stream=None, K: int = 0):
     """(F, dF/dV) for the grid's current state and potential; the grid ends at
-    psi_T.  dF/dV is returned as an (ny, nx) float32 CUDA tensor."""
+    psi_T.  dF/dV is returned as an (ny, nx) float32 CUDA tensor.  K is the
+    fused depth of the backward pass's launches (0: the library default)."""
     torch = _torch()
     st = stream or current_stream_ptr()
     tp, tdt, tw, keep_t = _array_ptr(target_re, grid.shape)
@@ -486,8 +492,14 @@ def adjoint_fidelity_grad(grid, target_re, target_im, steps: int, ckpt_every: in
     nbytes = ts_adjoint_workspace(grid.handle, int(steps), int(ckpt_every))
     ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     grad = torch.empty(grid.shape, dtype=torch.float32, device="cuda")
-    F = ts_adjoint_grad(grid.handle, tp, ip, tdt, tw, int(steps), int(ckpt_every),
-                        _VP(ws.data_ptr()), nbytes, _VP(grad.data_ptr()), st)
+    if K == 0:
+        F = ts_adjoint_grad(grid.handle, tp, ip, tdt, tw, int(steps), int(ckpt_every),
+                            _VP(ws.data_ptr()), nbytes, _VP(grad.data_ptr()), st)
+    else:
+        F, _ = ts_adjoint_forward(grid.handle, tp, ip, tdt, tw, int(steps), int(ckpt_every),
+                                  _VP(ws.data_ptr()), nbytes, st)
+        ts_adjoint_backward_depth(grid.handle, _VP(ws.data_ptr()), nbytes, int(K),
+                                  _VP(grad.data_ptr()), st)
     del keep_t, keep_i
     return F, grad
 
