@@ -761,7 +761,6 @@ ts_status fused_run(ts_grid *g, int64_t steps, int K, const ts::RotCoef &c,
         a.out_im = (float *)g->im_other();
         a.nx = (int)g->L.nx;
         a.ny = (int)g->rows();
-        a.ny_slab = g->is3d() ? (int)g->L.ny : 0;
         a.pitch = g->L.pitch;
         a.t1 = (float)c.t1;
         a.s1 = (float)c.s1;
@@ -800,34 +799,37 @@ ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
 // neighbouring steps run back to back (a run of 2 at either end, of 4
 // between two b substeps), so on the fused path each run of r substeps is
 // ceil(r / K) launches of near-equal depth; each b substep is one launch.
-// 3-D steps on the fast path (FP32, |theta| <= pi/4, even ny, ny < 2^16).
-// Z factors commute with X and Y factors, so the step
+// 3-D steps on the fast path (FP32, |theta| <= pi/4, (nz + 16) ny < 2^31):
+// one launch and one HBM round trip per step (fused.cu, fused3d_kernel).  Z
+// factors commute with X and Y factors, so the step
 //   Xe Xo Ye Yo Ze Zo P Zo Ze Yo Ye Xo Xe
-// equals Ze Zo [Xe Xo Ye Yo P Yo Ye Xo Xe] Zo Ze: a Z pass, the 2-D step
-// with Y pairs kept inside slabs (fused kernel at depth 1), a Z pass.  The Z
-// halves of neighbouring steps merge, Zo Ze Ze Zo = Zo Ze(2 theta) Zo, so n
-// steps take n + 1 Z passes (each one streaming pass over HBM).
+// equals Ze Zo [Xe Xo Ye Yo P Yo Ye Xo Xe] Zo Ze: each slab runs the depth-1
+// 2-D step with Y pairs kept inside it, its rows taking Ze, Zo as they enter
+// and Zo, Ze as they leave, in trade with the neighbouring slabs' rows.
 ts_status evolve3_fused(ts_grid *g, int64_t steps, cudaStream_t st)
 {
-    const int nx = (int)g->L.nx, ny = (int)g->L.ny, nz = (int)g->L.nz;
-    const float t1 = (float)g->t1, s1 = (float)g->s1, t2 = (float)g->t2, s2 = (float)g->s2;
-    const ts::ZSeq first = {2, {0, 1, 0}, {t1, t1, 0.f}, {s1, s1, 0.f}};
-    const ts::ZSeq mid = {3, {1, 0, 1}, {t1, t2, t1}, {s1, s2, s1}};
-    const ts::ZSeq last = {2, {1, 0, 0}, {t1, t1, 0.f}, {s1, s1, 0.f}};
-    auto zpass = [&](const ts::ZSeq &q) -> ts_status {
-        cudaError_t e = ts::launch_zstream((const float *)g->re(), (const float *)g->im(),
-                                           (float *)g->re_other(), (float *)g->im_other(), nx, ny,
-                                           nz, g->L.pitch, q, st);
-        if (e != cudaSuccess) return cuda_fail(e, "z-stream kernel launch");
+    if (!g->tmaps_ok) return fail(TS_ERR_STATE, "fused path: tensor maps missing");
+    const ts::RotCoef c = grid_coef(g);
+    for (int64_t n = 0; n < steps; ++n) {
+        ts::FusedLaunch a;
+        a.tm_state = &g->tm_state[g->cur];
+        a.tm_phase = &g->tm_phase;
+        a.out_re = (float *)g->re_other();
+        a.out_im = (float *)g->im_other();
+        a.nx = (int)g->L.nx;
+        a.ny = (int)g->L.ny;
+        a.pitch = g->L.pitch;
+        a.t1 = (float)c.t1;
+        a.s1 = (float)c.s1;
+        a.g1 = (float)c.g1;
+        a.t2 = (float)c.t2;
+        a.s2 = (float)c.s2;
+        a.err = g->err;
+        cudaError_t e = ts::launch_fused3d(a, (int)g->L.nz, st);
+        if (e != cudaSuccess) return cuda_fail(e, "3-D fused kernel launch");
         g->cur ^= 1;
-        return TS_OK;
-    };
-    ts_status s = zpass(first);
-    for (int64_t n = 0; n < steps && s == TS_OK; ++n) {
-        s = fused_run(g, 1, 1, grid_coef(g), &g->tm_phase, st);
-        if (s == TS_OK) s = zpass(n + 1 < steps ? mid : last);
     }
-    return s;
+    return TS_OK;
 }
 
 // Steps with the time-dependent potential V0 + a_n V1: the next `steps`
@@ -965,7 +967,8 @@ ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
         return evolve_f64(g, steps, st);
     }
     if (g->is3d()) {
-        if (std::fabs(g->theta) > 0.25 * M_PI || (g->L.ny & 1) || g->L.ny > 65535)
+        // (TMA row coordinates reach (nz + 14) ny: the last z-block's halo slabs)
+        if (std::fabs(g->theta) > 0.25 * M_PI || (g->L.nz + 16) * g->L.ny >= (int64_t(1) << 31))
             return plain_steps(g, steps, st);
         return evolve3_fused(g, steps, st);
     }

@@ -116,6 +116,12 @@ namespace {
 #ifndef TS_FUSED_ADJ_PF          // backward adjoint steps: row pairs of G prefetched into
 #define TS_FUSED_ADJ_PF 2        // L2 ahead of their plain loads (0: none)
 #endif
+#ifndef TS_FUSED_DRIVE_WARP_BRANCH   // drive phase: pick the short or the reduced series
+#define TS_FUSED_DRIVE_WARP_BRANCH 1     // per warp (1) or per lane (0)
+#endif
+#ifndef TS_FUSED3D_WARPS         // 3-D steps: warps per CTA (two slabs each); the CTA's
+#define TS_FUSED3D_WARPS 8       // first and last warp hold halo slabs
+#endif
 #ifndef TS_FUSED_PF_DUAL         // row pairs prefetched ahead of use by the backward
 #define TS_FUSED_PF_DUAL 2       // adjoint steps (two states per slot)
 #endif
@@ -135,10 +141,15 @@ constexpr uint32_t FULL = 0xffffffffu;
 // V1.  The fused fourth-order step (MODE 4) keeps the a substep's table in
 // the phase ring and the b substep's in a third, shorter ring (the b ring):
 // only substep 2 reads it, at iterations j + 2 and j + 3 of row pair j.
-__host__ __device__ constexpr int phase_planes(int mode) { return mode == 3 ? 3 : 2; }
+// MODE 6 (3-D steps) holds the rows of two slabs per slot: (gamma_V, s_V) of
+// each in the phase ring, (re, im) of each in the state ring.
+__host__ __device__ constexpr int phase_planes(int mode)
+{
+    return mode == 3 ? 3 : mode == 6 ? 4 : 2;
+}
 // Planes of a state-ring slot: (re, im); the backward adjoint steps (MODE 5)
 // carry two states, the forward state psi and the costate lambda.
-__host__ __device__ constexpr int state_planes(int mode) { return mode == 5 ? 4 : 2; }
+__host__ __device__ constexpr int state_planes(int mode) { return mode == 5 || mode == 6 ? 4 : 2; }
 
 // __launch_bounds__ minimum resident blocks of the single-grid kernel; the
 // backward adjoint steps (MODE 5) carry two states and K - 1 running sums of
@@ -159,10 +170,14 @@ __host__ __device__ constexpr int multi_min_blocks(int K)
                     : TS_FUSED_MIN_BLOCKS;
 }
 
-template <int K, int PP = 2, bool BRING = false, int SP = 2>
+template <int K, int PP = 2, bool BRING = false, int SP = 2, int M = 0>
 struct Cfg {
-    static constexpr int WPC = K <= 2 ? TS_FUSED_WPC_SHALLOW : TS_FUSED_WPC_DEEP;
-    static constexpr int PF = SP == 4 ? TS_FUSED_PF_DUAL
+    // MODE 6 (3-D steps): one CTA of TS_FUSED3D_WARPS warps, one slab each
+    static constexpr int WPC = M == 6 ? TS_FUSED3D_WARPS
+                               : K <= 2 ? TS_FUSED_WPC_SHALLOW
+                                        : TS_FUSED_WPC_DEEP;
+    static constexpr int PF = M == 6   ? 1
+                              : SP == 4 ? TS_FUSED_PF_DUAL
                               : K == 1 ? TS_FUSED_PF_K1
                               : K == 2 ? TS_FUSED_PF_K2
                                        : TS_FUSED_PF_DEEP;
@@ -182,12 +197,15 @@ struct Cfg {
     static constexpr int NBAR = NSS + NSP + NSB;   // mbarriers per warp
     static constexpr int SSLOT = SP * PLANE_SLOT_BYTES;   // a state slot
     static constexpr int WARP_SMEM = NSS * SSLOT + NSP * PSLOT + NSB * SLOT_BYTES;
-    static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + NBAR * 8);
+    // MODE 6: two buffers through which the CTA's warps trade their rows for
+    // the odd Z sweeps (a row pair of re, im of both slabs per warp: 4 KiB)
+    static constexpr int ZX_BYTES = M == 6 ? 2 * WPC * 4 * PLANE_SLOT_BYTES : 0;
+    static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + NBAR * 8) + ZX_BYTES;
 };
 
 // The configuration of a mode's kernel at depth K.
 template <int K, int MODE>
-using CfgM = Cfg<K, phase_planes(MODE), MODE == 4, state_planes(MODE)>;
+using CfgM = Cfg<K, phase_planes(MODE), MODE == 4, state_planes(MODE), MODE>;
 
 // Four columns of one row of one state, held by one lane.
 struct Frag {
@@ -195,14 +213,16 @@ struct Frag {
 };
 
 // The same columns of two states that take the same factors: the forward
-// state psi (a) and the costate lambda (b) of a backward adjoint step.
+// state psi (a) and the costate lambda (b) of a backward adjoint step, or
+// (MODE 6) the same row of two neighbouring slabs, z (a) and z + 1 (b).
 struct Frag2 {
     Frag a, b;
 };
 
-// The per-lane state of a mode: one state, or two for the backward steps.
+// The per-lane state of a mode: one state, or two for the backward adjoint
+// steps and the 3-D steps.
 template <int MODE>
-using StateT = std::conditional_t<MODE == 5, Frag2, Frag>;
+using StateT = std::conditional_t<MODE == 5 || MODE == 6, Frag2, Frag>;
 
 struct KParams {
     float *out_re, *out_im;
@@ -212,8 +232,6 @@ struct KParams {
     int64_t units;
     int total_warps;
     int strip_warps;         // > 0: warps per strip of the strip-aligned split
-    int ny_slab;             // > 0: a 3-D grid of ny / ny_slab slabs; no Y pair
-                             // crosses a slab boundary (ny_slab even)
     float t1, s1, g1, t2, s2;
     int *err;
     // MODE 5 (backward adjoint steps): the costate's output planes (out_re,
@@ -224,6 +242,10 @@ struct KParams {
     // and added into G once.
     float *out2_re, *out2_im;
     float *g_rh, *g_rl, *g_ih, *g_il;
+    // MODE 6 (3-D steps): slabs, z-blocks, row ranges per slab; ny is a
+    // slab's rows and out_re, out_im point at slab z of the output planes,
+    // out2_re, out2_im at slab z + 1 (the warp's two slabs)
+    int nz, n_zblocks, n_ranges;
     // MODE 3 (time-dependent potential V0 + a(t) V1): a_n dt / 2 of step k
     // of the launch; the phase ring carries V1 as a third plane
     float adt[FUSED_MAX_K];
@@ -422,11 +444,13 @@ __device__ __forceinline__ void versine_short2(float2 h, float2 &g, float2 &s)
 template <bool PACKED>
 __device__ __forceinline__ void drive4(Frag &f, float4 v1, float hdt)
 {
-    // hdt = a_n dt / 2: the half angles of the lane's four columns; one
-    // branch per lane picks the short series when all four are small
+    // hdt = a_n dt / 2: the half angles of the lane's four columns; the
+    // short series serves when all of them are small -- in every lane of the
+    // warp, so that the branch does not diverge (all lanes are converged here)
     const float4 h = make_float4(hdt * v1.x, hdt * v1.y, hdt * v1.z, hdt * v1.w);
     float4 g, s;
-    if (fmaxf(fmaxf(fabsf(h.x), fabsf(h.y)), fmaxf(fabsf(h.z), fabsf(h.w))) <= 0.4f) {
+    const bool small_h = fmaxf(fmaxf(fabsf(h.x), fabsf(h.y)), fmaxf(fabsf(h.z), fabsf(h.w))) <= 0.4f;
+    if (TS_FUSED_DRIVE_WARP_BRANCH ? __all_sync(FULL, small_h) : small_h) {
         if constexpr (PACKED) {
             float2 g0, s0, g1, s1;
             versine_short2(lo2(h), g0, s0);
@@ -603,8 +627,7 @@ __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2
     auto is_b = [](int k) { return MODE == 4 && k == 2; };
     constexpr int NSP = C::NSP;
     auto yok = [&](int y) {
-        return INTERIOR ||
-               (y >= 0 && y + 1 < p.ny && (p.ny_slab == 0 || (y + 1) % p.ny_slab != 0));
+        return INTERIOR || (y >= 0 && y + 1 < p.ny);
     };
     auto slot_p = [&](int back) -> const unsigned char * {   // phase slot j - back
         int q = pos_p - back;
@@ -632,20 +655,22 @@ __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2
     int y1 = yin - 1;
     Frag carP, carQ;   // MODE 5: running sums handed from step k - 1 to step k
     if constexpr (MODE == 5) adj_step<K>(0, P, Q, y1, acc, carP, carQ, w, p);
+    // the phase of step k on one row from phase slot sp (row 0 or 1 of the
+    // slot): conjugated in a backward step (exp(+i V dt) has sine -s_V); with
+    // the drive term for MODE 3; MODE 6 holds two slabs, each with its table
+    auto phase_row = [&](S &X, const unsigned char *sp, int row, int k) {
+        if constexpr (MODE == 6) {
+            phase4<C::PACKED>(X.a, lds4(sp, 0, row, lane), lds4(sp, 1, row, lane));
+            phase4<C::PACKED>(X.b, lds4(sp, 2, row, lane), lds4(sp, 3, row, lane));
+        } else {
+            const float4 sv = lds4(sp, 1, row, lane);
+            phase4<C::PACKED>(X, lds4(sp, 0, row, lane), CONJ ? neg4(sv) : sv);
+            if constexpr (MODE == 3) drive4<C::PACKED>(X, lds4(sp, 2, row, lane), p.adt[k]);
+        }
+    };
     // phase of step 0 on rows (y1, y1+1): slot j-1 row 1, slot j row 0
-    // (conjugated in a backward step: exp(+i V dt) has sine -s_V)
-    if (INTERIOR || j >= 1) {
-        const unsigned char *sp = slot_p(1);
-        const float4 sv = lds4(sp, 1, 1, lane);
-        phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), CONJ ? neg4(sv) : sv);
-        if constexpr (MODE == 3) drive4<C::PACKED>(P, lds4(sp, 2, 1, lane), p.adt[0]);
-    }
-    {
-        const unsigned char *sp = slot_p(0);
-        const float4 sv = lds4(sp, 1, 0, lane);
-        phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), CONJ ? neg4(sv) : sv);
-        if constexpr (MODE == 3) drive4<C::PACKED>(Q, lds4(sp, 2, 0, lane), p.adt[0]);
-    }
+    if (INTERIOR || j >= 1) phase_row(P, slot_p(1), 1, 0);
+    phase_row(Q, slot_p(0), 0, 0);
 #pragma unroll
     for (int k = 1; k < K; ++k) {
         // angles of the two steps that meet here (MODE 4: a or b) and of
@@ -686,18 +711,8 @@ __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2
         // (MODE 4: the b substep's table comes from the b ring; MODE 5: the
         // conjugate phase, sine -s_V)
         auto slot_k = [&](int back) { return bk ? slot_b(back) : slot_p(back); };
-        if (INTERIOR || j - k - 1 >= 0) {
-            const unsigned char *sp = slot_k(k + 1);
-            const float4 sv = lds4(sp, 1, 1, lane);
-            phase4<C::PACKED>(P, lds4(sp, 0, 1, lane), CONJ ? neg4(sv) : sv);
-            if constexpr (MODE == 3) drive4<C::PACKED>(P, lds4(sp, 2, 1, lane), p.adt[k]);
-        }
-        if (INTERIOR || j - k >= 0) {
-            const unsigned char *sp = slot_k(k);
-            const float4 sv = lds4(sp, 1, 0, lane);
-            phase4<C::PACKED>(Q, lds4(sp, 0, 0, lane), CONJ ? neg4(sv) : sv);
-            if constexpr (MODE == 3) drive4<C::PACKED>(Q, lds4(sp, 2, 0, lane), p.adt[k]);
-        }
+        if (INTERIOR || j - k - 1 >= 0) phase_row(P, slot_k(k + 1), 1, k);
+        if (INTERIOR || j - k >= 0) phase_row(Q, slot_k(k), 0, k);
     }
     // last step, second half: Yo aligned, Ye shifted, Xo, Xe
     {
@@ -731,10 +746,10 @@ struct WarpRings {
     int cnt_b;
 };
 
-template <int K, int PP = 2, bool BRING = false, int SP = 2>
+template <int K, int PP = 2, bool BRING = false, int SP = 2, int M = 0>
 __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int warp, int lane)
 {
-    using C = Cfg<K, PP, BRING, SP>;
+    using C = Cfg<K, PP, BRING, SP, M>;
     constexpr int NSS = C::NSS, NSP = C::NSP, NBAR = C::NBAR;
     WarpRings r;
     // barriers first, then 1 KiB-aligned slots (state ring, phase ring, b ring)
@@ -766,16 +781,35 @@ __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int wa
 struct Seg {
     const CUtensorMap *tm_state, *tm_phase, *tm_b, *tm_x;   // MODE 5: tm_x the G planes
     int XL, xg, Y0, Y1, Ys, n_iter, lane;
+    int ytma;                // added to row coordinates of TMA copies (MODE 6: z ny)
+    int yslab;               // MODE 6: rows from slab z to slab z + 1
     bool store_lane;
     StripCoef c;
     Owned own;
+    // MODE 6: the warp's lower slab z (even), its index in the CTA, the Z
+    // exchange buffers, and which of its two slabs (z, z + 1) it writes
+    int z, w;
+    float4 *zx;
+    bool store_a, store_b;
 };
 
-template <int SSLOT>
+// MODE 6: where a warp sits in its CTA's block of slabs.
+struct Slab3 {
+    int z = 0, w = 0, ytma = 0;
+    float4 *zx = nullptr;
+    bool store_a = true, store_b = true;
+};
+
+// MODE 6 (TWO): one slot takes the rows of slab z and then those of slab
+// z + 1 (yslab rows further on), two copies on one mbarrier.
+template <int SSLOT, bool TWO = false>
 __device__ __forceinline__ void issue_state(WarpRings &r, const Seg &s, int pos, int j)
 {
     mbar_expect_tx(&r.bar_s[pos], SSLOT);
-    tma_load_pair(r.ring_s + pos * SSLOT, s.tm_state, s.XL, s.Ys + 2 * j, &r.bar_s[pos]);
+    unsigned char *dst = r.ring_s + pos * SSLOT;
+    const int y = s.ytma + s.Ys + 2 * j;
+    tma_load_pair(dst, s.tm_state, s.XL, y, &r.bar_s[pos]);
+    if constexpr (TWO) tma_load_pair(dst + SSLOT / 2, s.tm_state, s.XL, y + s.yslab, &r.bar_s[pos]);
 }
 
 // b ring (MODE 4): the b substep's (gamma, s) rows of row pair j, copy
@@ -795,12 +829,76 @@ __device__ __forceinline__ bool wait_b(const WarpRings &r, int j, uint64_t limit
     return mbar_wait(&r.bar_b[L % NSB], (uint32_t)(L / NSB) & 1u, limit);
 }
 
-template <int K, int PP = 2>
+template <int K, int PP = 2, bool TWO = false>
 __device__ __forceinline__ void issue_phase(WarpRings &r, const Seg &s, int pos, int j)
 {
     constexpr int PSLOT = Cfg<K, PP>::PSLOT;
     mbar_expect_tx(&r.bar_p[pos], PSLOT);
-    tma_load_pair(r.ring_p + pos * PSLOT, s.tm_phase, s.XL, s.Ys + 2 * j, &r.bar_p[pos]);
+    unsigned char *dst = r.ring_p + pos * PSLOT;
+    const int y = s.ytma + s.Ys + 2 * j;
+    tma_load_pair(dst, s.tm_phase, s.XL, y, &r.bar_p[pos]);
+    if constexpr (TWO) tma_load_pair(dst + PSLOT / 2, s.tm_phase, s.XL, y + s.yslab, &r.bar_p[pos]);
+}
+
+// MODE 6: the Z sweeps of the two rows (r0, r1) that every warp of the CTA
+// holds at the same y; warp w holds slabs z = z_w (even, in .a) and z + 1
+// (in .b).  Even Z pairs (z, z + 1) lie inside a warp: a register rotation
+// (lifting form).  Odd pairs (z + 1, z + 2) and (z - 1, z) join neighbouring
+// warps: each warp puts its rows in exchange buffer `zbuf`, the CTA meets at
+// a barrier, and each warp updates its own members from their partners' old
+// values in the versine form (a' = a - g a + i s b).  The two buffers
+// alternate, so that a warp writing the next exchange cannot overwrite rows
+// another warp still reads (it has passed the next barrier first).  A pair
+// needs both slabs on the grid and both in the CTA.
+__device__ __forceinline__ bool on_grid(int z, const KParams &p) { return z >= 0 && z < p.nz; }
+
+template <bool PACKED>
+__device__ __forceinline__ void z_even(Frag2 &r0, Frag2 &r1, const Seg &s, const KParams &p)
+{
+    const bool v = on_grid(s.z, p) && on_grid(s.z + 1, p);
+    y_pair<PACKED>(r0.a, r0.b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+    y_pair<PACKED>(r1.a, r1.b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
+}
+
+template <int NW>
+__device__ __forceinline__ void z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const KParams &p,
+                                      int &zbuf)
+{
+    const int lane = s.lane;
+    float4 *mine = s.zx + (zbuf * NW + s.w) * 256;
+    mine[lane] = r0.a.re;
+    mine[32 + lane] = r0.a.im;
+    mine[64 + lane] = r1.a.re;
+    mine[96 + lane] = r1.a.im;
+    mine[128 + lane] = r0.b.re;
+    mine[160 + lane] = r0.b.im;
+    mine[192 + lane] = r1.b.re;
+    mine[224 + lane] = r1.b.im;
+    __syncthreads();
+    const float g = p.g1, sn = p.s1;
+    const float2 ng = make_float2(-g, -g), ns = make_float2(-sn, -sn), ps = make_float2(sn, sn);
+    auto one = [&](Frag &f, const float4 *q, int row) {   // f <- f - g f + i s q, four columns
+        const float4 qr = q[64 * row + lane], qi = q[64 * row + 32 + lane];
+        const float2 r0n = __ffma2_rn(ns, lo2(qi), __ffma2_rn(ng, lo2(f.re), lo2(f.re)));
+        const float2 m0n = __ffma2_rn(ps, lo2(qr), __ffma2_rn(ng, lo2(f.im), lo2(f.im)));
+        const float2 r1n = __ffma2_rn(ns, hi2(qi), __ffma2_rn(ng, hi2(f.re), hi2(f.re)));
+        const float2 m1n = __ffma2_rn(ps, hi2(qr), __ffma2_rn(ng, hi2(f.im), hi2(f.im)));
+        f.re = join2(r0n, r1n);
+        f.im = join2(m0n, m1n);
+    };
+    // slab z + 1 with the next warp's slab z + 2 (its .a rows)
+    if (s.w + 1 < NW && on_grid(s.z + 1, p) && on_grid(s.z + 2, p)) {
+        const float4 *q = s.zx + (zbuf * NW + s.w + 1) * 256;
+        one(r0.b, q, 0);
+        one(r1.b, q, 1);
+    }
+    // slab z with the previous warp's slab z - 1 (its .b rows)
+    if (s.w > 0 && on_grid(s.z - 1, p) && on_grid(s.z, p)) {
+        const float4 *q = s.zx + (zbuf * NW + s.w - 1) * 256 + 128;
+        one(r0.a, q, 0);
+        one(r1.a, q, 1);
+    }
+    zbuf ^= 1;
 }
 
 // Row pair j of a segment: wait for its slots, run the pipeline, store the
@@ -824,6 +922,8 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     if constexpr (MODE == 4)   // row pair j - 2's b rows, first read now
         ok = ok && (j < 2 || wait_b<NSB>(r, j - 2, WAIT_LIMIT_NS));
     ok = __all_sync(FULL, ok);
+    // MODE 6: the CTA's warps meet at barriers, so they give up together
+    if constexpr (MODE == 6) ok = !__syncthreads_or(!ok);
     if (!ok) {
         if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
         // drain this warp's outstanding copies (bounded) before leaving
@@ -862,19 +962,36 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
         }
     };
     S a, b;
-    if constexpr (MODE == 5) {
+    if constexpr (MODE == 5 || MODE == 6) {
         load_rows(a.a, b.a, 0);
         load_rows(a.b, b.b, 2);
     } else {
         load_rows(a, b, 0);
     }
+    // MODE 6: a 3-D step is Ze Zo [the 2-D step] Zo Ze (Z factors commute
+    // with X and Y factors): the rows entering the pipeline take Ze, Zo, the
+    // rows leaving it take Zo, Ze.  (Between row pairs the CTA meets at the
+    // barrier of the wait decision above, so each row pair may start with
+    // buffer 0.)
+    int zbuf = 0;
+    if constexpr (MODE == 6) {
+        z_even<C::PACKED>(a, b, s, p);
+        z_odd<C::WPC>(a, b, s, p, zbuf);
+    }
     const int yin = s.Ys + 2 * j;
     S O0, O1;
     pipeline_step<K, INTERIOR, MODE>(cin, cout, acc, a, b, yin, j, r.ring_p, r.pos_p, r.ring_b,
                                      r.cnt_b, s.c, p, lane, s.own, O0, O1);
+    if constexpr (MODE == 6) {
+        z_odd<C::WPC>(O0, O1, s, p, zbuf);
+        z_even<C::PACKED>(O0, O1, s, p);
+    }
     const int yo = yin - 2 * K;
     if (s.store_lane && yo >= s.Y0 && yo < s.Y1) {
-        if constexpr (MODE == 5) {
+        if constexpr (MODE == 6) {
+            if (s.store_a) store_rows(O0.a, O1.a, p.out_re, p.out_im, yo);
+            if (s.store_b) store_rows(O0.b, O1.b, p.out2_re, p.out2_im, yo);
+        } else if constexpr (MODE == 5) {
             store_rows(O0.a, O1.a, p.out_re, p.out_im, yo);
             store_rows(O0.b, O1.b, p.out2_re, p.out2_im, yo);
         } else {
@@ -890,9 +1007,9 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     const bool more_b = MODE == 4 && j >= 3 && jb < s.n_iter;
     if (lane == 0 && (more_s || more_p || more_b)) {
         fence_proxy_async();
-        if (more_s) issue_state<C::SSLOT>(r, s, r.pos_s, js);
+        if (more_s) issue_state<C::SSLOT, MODE == 6>(r, s, r.pos_s, js);
         if (more_p)
-            issue_phase<K, phase_planes(MODE)>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
+            issue_phase<K, phase_planes(MODE), MODE == 6>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
         if constexpr (MODE == 4) {
             if (more_b) issue_b<NSB>(r, s, jb);   // the slot row pair j - 3 leaves
         }
@@ -919,7 +1036,7 @@ template <int K, int MODE>
 __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_state,
                                             const CUtensorMap *tm_phase, const CUtensorMap *tm_b,
                                             const CUtensorMap *tm_x, const KParams &p, int sx,
-                                            int q0, int q1, int lane)
+                                            int q0, int q1, int lane, const Slab3 &sl = Slab3())
 {
     using C = CfgM<K, MODE>;
     using S = StateT<MODE>;
@@ -930,6 +1047,13 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     s.tm_phase = tm_phase;
     s.tm_b = tm_b;
     s.tm_x = tm_x;
+    s.ytma = sl.ytma;
+    s.yslab = p.ny;
+    s.z = sl.z;
+    s.w = sl.w;
+    s.zx = sl.zx;
+    s.store_a = sl.store_a;
+    s.store_b = sl.store_b;
     s.lane = lane;
     s.XL = sx * VALID - HALO;            // first loaded column (multiple of 4)
     s.xg = s.XL + 4 * lane;              // this lane's first column
@@ -961,8 +1085,8 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     if (lane == 0) {
         fence_proxy_async();
         for (int j = 0; j < n_pro_p; ++j) {
-            if (j < n_pro_s) issue_state<C::SSLOT>(r, s, (r.pos_s + j) % NSS, j);
-            issue_phase<K, phase_planes(MODE)>(r, s, (r.pos_p + j) % NSP, j);
+            if (j < n_pro_s) issue_state<C::SSLOT, MODE == 6>(r, s, (r.pos_s + j) % NSS, j);
+            issue_phase<K, phase_planes(MODE), MODE == 6>(r, s, (r.pos_p + j) % NSP, j);
             if constexpr (MODE == 4) {
                 if (j < n_pro_b) issue_b<NSB>(r, s, j);
             }
@@ -986,8 +1110,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     }
     auto interior = [&](int j) {
         const int yin = s.Ys + 2 * j;
-        return j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny &&
-               (p.ny_slab == 0 || (yin - 2 * K) / p.ny_slab == (yin + 1) / p.ny_slab);
+        return j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny;
     };
     for (int j = 0; j < s.n_iter;) {
         if (j + 1 < s.n_iter && interior(j) && interior(j + 1)) {
@@ -1035,7 +1158,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * Cfg<K>::WPC + warp;
     if (gw >= p.total_warps) return;
-    WarpRings r = carve_rings<K, phase_planes(MODE), MODE == 4, state_planes(MODE)>(smem_raw, warp, lane);
+    WarpRings r = carve_rings<K, phase_planes(MODE), MODE == 4, state_planes(MODE), MODE>(smem_raw, warp, lane);
     if (p.strip_warps > 0) {
         // strip-aligned split: warp (sx, i) takes row range i of strip sx, so
         // warps of neighbouring strips walk the same rows at the same time and
@@ -1055,6 +1178,64 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
         const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
         u += q1 - q0;
         if (!run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, &tm_x, p, sx, q0, q1, lane)) return;
+    }
+}
+
+// Three-dimensional steps, one step per launch, one HBM round trip.  A CTA
+// owns a block of 2 TS_FUSED3D_WARPS consecutive slabs of one strip and one
+// range of rows; warp w runs the depth-1 pipeline on slabs z and z + 1,
+// z = zb * VZ - 2 + 2 w (even), and all warps walk the same rows together.
+// The rows entering the pipeline take Ze (inside the warp) and Zo (traded
+// with the neighbouring warps), the rows leaving it Zo and Ze.  The two
+// slabs at either end of the block lack partners outside it: they are a
+// halo, computed but not stored (with the block's first slab even, two per
+// side are enough for the four Z sweeps of a step), so a CTA stores
+// VZ = 2 NW - 4 slabs.  Slabs outside the grid are zero rows from TMA and
+// pair with nothing.  Units (z-block fastest, then strip, then row range) go
+// round robin over the resident CTAs, so the CTAs of neighbouring z-blocks
+// run together and read their shared halo slabs through L2.
+template <int K>
+__global__ void __launch_bounds__(TS_FUSED3D_WARPS * 32, 1)
+fused3d_kernel(const __grid_constant__ CUtensorMap tm_state,
+               const __grid_constant__ CUtensorMap tm_phase, const KParams p)
+{
+    static_assert(K == 1, "3-D steps run one step per launch");
+    using C = CfgM<K, 6>;
+    constexpr int NW = C::WPC, VZ = 2 * NW - 4;
+    static_assert(VZ > 0 && VZ % 2 == 0, "the block's first slab must stay even");
+    extern __shared__ unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpRings r = carve_rings<K, phase_planes(6), false, state_planes(6), 6>(smem_raw, warp, lane);
+    const uint32_t base_addr = smem_addr(smem_raw);
+    const uint32_t slots_off = ((base_addr + NW * C::NBAR * 8 + 1023u) & ~1023u) - base_addr;
+    float4 *zx = reinterpret_cast<float4 *>(smem_raw + slots_off + (size_t)NW * C::WARP_SMEM);
+    const int64_t slab = (int64_t)p.ny * p.pitch;
+    for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
+        const int zb = (int)(u % p.n_zblocks);
+        const int64_t t = u / p.n_zblocks;
+        const int sx = (int)(t % p.n_strips), rr = (int)(t / p.n_strips);
+        const int q0 = (int)((int64_t)rr * p.n_pairs / p.n_ranges);
+        const int q1 = (int)((int64_t)(rr + 1) * p.n_pairs / p.n_ranges);
+        if (q1 <= q0) continue;                  // the same for every warp of the CTA
+        Slab3 sl;
+        sl.z = zb * VZ - 2 + 2 * warp;
+        sl.w = warp;
+        sl.ytma = sl.z * p.ny;
+        sl.zx = zx;
+        const bool inner = warp >= 1 && warp < NW - 1;
+        sl.store_a = inner && sl.z >= 0 && sl.z < p.nz;
+        sl.store_b = inner && sl.z + 1 >= 0 && sl.z + 1 < p.nz;
+        KParams pw = p;
+        if (sl.store_a) {
+            pw.out_re = p.out_re + sl.z * slab;
+            pw.out_im = p.out_im + sl.z * slab;
+        }
+        if (sl.store_b) {
+            pw.out2_re = p.out_re + (sl.z + 1) * slab;
+            pw.out2_im = p.out_im + (sl.z + 1) * slab;
+        }
+        if (!run_segment<K, 6>(r, &tm_state, &tm_phase, nullptr, nullptr, pw, sx, q0, q1, lane, sl))
+            return;
     }
 }
 
@@ -1084,7 +1265,6 @@ __device__ __forceinline__ void multi_params(KParams &p, const GridDesc *d, int 
     p.err = err;
     p.n_pairs = (p.ny + 1) / 2;
     p.strip_warps = 0;
-    p.ny_slab = 0;
 }
 
 template <int K>
@@ -1179,6 +1359,47 @@ inline int64_t min_pairs_per_warp(int64_t units, int num_sms)
 }
 
 template <typename F>
+Occupancy occupancy_of(F kernel, int threads, int smem);
+
+// One 3-D step over an nx x ny x nz FP32 grid (a.ny = ny rows per slab).
+cudaError_t launch3_k(const FusedLaunch &a, int nz, cudaStream_t st)
+{
+    using C = CfgM<1, 6>;
+    constexpr int NW = C::WPC, VZ = 2 * NW - 4;
+    static const Occupancy occ = occupancy_of(fused3d_kernel<1>, NW * 32, C::SMEM);
+    if (occ.err != cudaSuccess) return occ.err;
+    KParams p = {};
+    p.out_re = a.out_re;
+    p.out_im = a.out_im;
+    p.nx = a.nx;
+    p.ny = a.ny;
+    p.nz = nz;
+    p.pitch = a.pitch;
+    p.n_strips = (a.nx + C::VALID - 1) / C::VALID;
+    p.n_pairs = (a.ny + 1) / 2;
+    p.n_zblocks = (nz + VZ - 1) / VZ;
+    // enough row ranges for about four units per resident CTA, each range at
+    // least 16 row pairs long (its pipeline fill is 2 row pairs)
+    const int64_t ctas = (int64_t)occ.num_sms * occ.blocks_per_sm;
+    const int64_t blocks = (int64_t)p.n_strips * p.n_zblocks;
+    int64_t ranges = (4 * ctas + blocks - 1) / blocks;
+    ranges = std::max<int64_t>(1, std::min<int64_t>(ranges, p.n_pairs / 16));
+    p.n_ranges = (int)ranges;
+    p.units = blocks * ranges;
+    p.strip_warps = 0;
+    p.t1 = a.t1;
+    p.s1 = a.s1;
+    p.g1 = a.g1;
+    p.t2 = a.t2;
+    p.s2 = a.s2;
+    p.err = a.err;
+    const int grid = (int)std::min<int64_t>(p.units, ctas);
+    fused3d_kernel<1><<<grid, NW * 32, C::SMEM, st>>>(*a.tm_state, *a.tm_phase, p);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename F>
 Occupancy occupancy_of(F kernel, int threads, int smem)
 {
     Occupancy o = {cudaSuccess, 0, 0};
@@ -1222,7 +1443,6 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
         p.strip_warps = (int)w;
         p.total_warps = (int)(w * p.n_strips);
     }
-    p.ny_slab = a.ny_slab;
     p.t1 = a.t1;
     p.s1 = a.s1;
     p.g1 = a.g1;
@@ -1411,6 +1631,11 @@ cudaError_t launch_fused_drive(int K, const FusedLaunch &a, cudaStream_t st)
 }
 
 cudaError_t launch_fused_u4(const FusedLaunch &a, cudaStream_t st) { return launch_k<5, 4>(a, st); }
+
+cudaError_t launch_fused3d(const FusedLaunch &a, int nz, cudaStream_t st)
+{
+    return launch3_k(a, nz, st);
+}
 
 cudaError_t launch_fused_adjoint(int K, const FusedLaunch &a, cudaStream_t st)
 {

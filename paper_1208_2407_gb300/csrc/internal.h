@@ -61,17 +61,6 @@ cudaError_t launch_plain_sweep_y3(void *re, void *im, bool f64, int nx, int ny, 
 cudaError_t launch_plain_sweep_z(void *re, void *im, bool f64, int nx, int ny, int nz,
                                  int64_t pitch, int parity, double g, double s, cudaStream_t st,
                                  bool lift = false);
-// Up to three Z sweeps applied in one streaming pass over an FP32 grid,
-// from the planes (in_re, in_im) to (out_re, out_im): sweep i pairs slabs
-// (z, z+1) with z % 2 == parity[i], in lifting form (t[i], s[i]).
-struct ZSeq {
-    int m;
-    int parity[3];
-    float t[3], s[3];
-};
-cudaError_t launch_zstream(const float *in_re, const float *in_im, float *out_re, float *out_im,
-                           int nx, int ny, int nz, int64_t pitch, const ZSeq &q,
-                           cudaStream_t st);
 
 // --- observables (reduce.cu) ----------------------------------------------
 // partials: OBS_MAX_BLOCKS * OBS_Q doubles; result: OBS_Q doubles.
@@ -112,9 +101,6 @@ struct FusedLaunch {
     float *g_rh = nullptr, *g_rl = nullptr, *g_ih = nullptr, *g_il = nullptr;
     // time-dependent potential (launch_fused_drive only): a_n dt of step k
     float adt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    // 3-D grids: rows per slab (ny above counts all rows, slab by slab);
-    // 0 for 2-D grids
-    int ny_slab = 0;
     // the fused fourth-order step (launch_fused_u4): t1..s2 above are the
     // a substep's; the b substep's lifting (tb, sb) and versine (gb) forms,
     // and the merged angle a + b in lifting form (tab, sab)
@@ -140,6 +126,11 @@ cudaError_t launch_fused_drive(int K, const FusedLaunch &a, cudaStream_t st);
 // One fourth-order step U4 = a a b a a in one launch (five substeps, depth
 // 5): tm_phase maps the a substep's table, tm_b the b substep's.
 cudaError_t launch_fused_u4(const FusedLaunch &a, cudaStream_t st);
+// One 3-D step Xe Xo Ye Yo Ze Zo P Zo Ze Yo Ye Xo Xe over an nx x ny x nz
+// FP32 grid in one HBM round trip: a.ny is the rows of one slab, tm_state
+// and tm_phase map all ny * nz rows (slab after slab), out_re, out_im take
+// the result.  Needs (nz + 16) * ny < 2^31.
+cudaError_t launch_fused3d(const FusedLaunch &a, int nz, cudaStream_t st);
 
 // Device-resident description of one FP32 grid for the multi-grid launch
 // (written once per grid set-up; read by the kernel with generic loads, its

@@ -1,7 +1,9 @@
 """Three-dimensional lattices on the GPU vs the FP64 oracle's 3-D step,
-through the C ABI.  FP32 grids with even ny run a streaming Z pass and the
-slab-aware fused 2-D step in turn; odd ny, FP64 and ts_evolve_plain run one
-kernel per sweep.  Tolerances: FP64 1e-12, FP32 1e-5 relative L2.
+through the C ABI.  FP32 grids run one fused launch per step (a CTA per
+block of 16 slabs, two per warp, 12 of them stored, trading rows for the odd
+Z sweeps);
+FP64 and ts_evolve_plain run one kernel per sweep.  Tolerances: FP64 1e-12,
+FP32 1e-5 relative L2.
 """
 import os
 
@@ -78,12 +80,17 @@ def test_fp64_launch_count():
         g.close()
 
 
+# nz across the z-blocks of 12 stored slabs (2, 3, 11, 12, 13, 24, 25, 40,
+# 150), odd and even ny (1 and 2 included), strips of 120 columns with a
+# ragged last one (121, 241, 257)
 @pytest.mark.parametrize("nx,ny,nz", [(96, 64, 40), (130, 66, 17), (33, 2, 9), (257, 130, 5),
-                                      (64, 32, 150), (20, 8, 2), (5, 11, 7)])
+                                      (64, 32, 150), (20, 8, 2), (5, 11, 7), (121, 7, 13),
+                                      (40, 9, 3), (3, 1, 25), (241, 5, 24), (17, 12, 11),
+                                      (16, 3, 12)])
 @pytest.mark.parametrize("path", ["fused", "plain"])
 def test_fp32_matches_oracle(nx, ny, nz, path):
-    """Even ny takes the Z-pass + fused path (nz = 150 spans three Z
-    segments of 64 with their halos); odd ny falls back to the plain path."""
+    """Every side length and block edge of the fused 3-D step against the
+    oracle, and the plain path on the same lattices."""
     rng = np.random.default_rng(nx * 3 + ny * 5 + nz)
     re, im = rand3(rng, nx, ny, nz)
     V = rng.uniform(-0.5, 0.5, (nz, ny, nx))
@@ -114,7 +121,7 @@ def test_launch_sequence_and_refusals():
         g.set_potential(None, 0.05, 0.025)
         trotter.ts_launch_count(reset=True)
         g.evolve(5)
-        assert trotter.ts_launch_count() == 5 + 6      # n fused launches, n + 1 Z passes
+        assert trotter.ts_launch_count() == 5          # one fused launch per step
         with pytest.raises(trotter.TrotterError) as e:
             g.set_potential(None, 0.05, 0.025, order=4)
         assert e.value.status == trotter.TS_ERR_UNSUPPORTED
