@@ -57,6 +57,8 @@ def parse():
                     help="skip the FP32 / FP64 path comparison")
     ap.add_argument("--no-k-sweep", action="store_true",
                     help="skip the depth sweep (K = 1..8 at 8192^2 and 16384^2, plain paths)")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy block (FP64 oracle on the host: ~1-2 minutes)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint timing (1024^2 x 500 and 4096^2 x 200 steps)")
     ap.add_argument("--serve-requests", type=int, default=512)
@@ -654,6 +656,113 @@ def adjoint_bench(args, hbm_peak, cases=((1024, 500, 50), (4096, 200, 50)), dept
             "note": "inputs resident in HBM; median of %d runs per depth" % reps}
 
 
+def accuracy_block(args):
+    """The accuracy workloads against the FP64 oracle on this host's cores:
+    the 256^2 FP64 plain workload (100 steps); the 2048^2 FP32 harmonic
+    workload for seeds 0-4 (1000 steps: relative L2 error, norm drift, energy
+    drift beside the oracle's own drift, and the oracle's time), and seed 0 on
+    the FP64 path; the 1024^2 adjoint (500 steps, checkpoints every 50):
+    fidelity and gradient against central differences in FP64 on 64 sites
+    and against the oracle adjoint."""
+    import oracle
+    import torch
+    from paper_1208_2407_gb300 import trotter
+    from paper_1208_2407_gb300 import workloads as wl
+    cores = os.cpu_count() or 1
+    out = {"host_cores": cores}
+
+    def rel(are, aim, bre, bim):
+        return float(np.sqrt(np.sum((are - bre) ** 2 + (aim - bim) ** 2) /
+                             np.sum(bre ** 2 + bim ** 2)))
+
+    def gpu_run(c, dtype, plain=False):
+        g = trotter.Grid(c["nx"], c["ny"], dtype)
+        try:
+            g.set_state(c["re"], c["im"])
+            g.set_potential(c["V"], c["dt"], c["theta"])
+            o0 = g.observe()
+            (g.evolve_plain if plain else g.evolve)(c["steps"])
+            o1 = g.observe()
+            re, im = g.get_state(np.float64)
+        finally:
+            g.close()
+        return re, im, o0, o1
+
+    c = wl.plain_fp64_256()
+    gre, gim, _, o1 = gpu_run(c, "f64", plain=True)
+    t0 = time.perf_counter()
+    ore, oim = oracle.evolve(c["re"], c["im"], c["V"], c["dt"], c["theta"], c["steps"])
+    t_or = time.perf_counter() - t0
+    m = oracle.moments(ore, oim)
+    out["c1_plain_fp64_256"] = {
+        "rel_l2": rel(gre, gim, ore, oim), "norm_minus_1": o1["norm"] - 1.0,
+        "x_err": abs(o1["x"] - m[1] / m[0]), "y_err": abs(o1["y"] - m[2] / m[0]),
+        "oracle_site_steps_per_s_1thread": 256 * 256 * c["steps"] / t_or}
+
+    seeds = []
+    for seed in range(5):
+        c = wl.harmonic_2048(seed=seed)
+        gre, gim, o0, o1 = gpu_run(c, "f32")
+        t0 = time.perf_counter()
+        ore, oim = oracle.evolve(c["re"], c["im"], c["V"], c["dt"], c["theta"], c["steps"],
+                                 nthreads=cores)
+        t_or = time.perf_counter() - t0
+        e0 = sum(oracle.energy(c["re"], c["im"], c["V"]))
+        eo = sum(oracle.energy(ore, oim, c["V"]))
+        scale = max(1e-12, abs(e0))
+        row = {"seed": seed, "rel_l2": rel(gre, gim, ore, oim),
+               "norm_drift": abs(o1["norm"] - o0["norm"]),
+               "energy_drift_rel": (o1["e_kin"] + o1["e_pot"] - o0["e_kin"] - o0["e_pot"]) / scale,
+               "oracle_energy_drift_rel": (eo - e0) / scale,
+               "oracle_site_steps_per_s": float(c["nx"]) * c["ny"] * c["steps"] / t_or}
+        if seed == 0:
+            fre, fim, _, _ = gpu_run(c, "f64")
+            row["fp64_evolve_rel_l2"] = rel(fre, fim, ore, oim)
+        seeds.append(row)
+    out["c2_harmonic_2048_fp32"] = seeds
+
+    c = wl.adjoint_pair(n=1024, steps=500, seed=0)
+    g = trotter.Grid(c["nx"], c["ny"], "f32")
+    try:
+        g.set_state(c["re"], c["im"])
+        g.set_potential(c["V"], c["dt"], c["theta"])
+        F, grad = trotter.adjoint_fidelity_grad(g, c["target_re"], c["target_im"], c["steps"], 50)
+        grad = grad.double().cpu().numpy()
+    finally:
+        g.close()
+    rng = np.random.default_rng(123)
+    weight = c["re"] ** 2 + c["im"] ** 2 + c["target_re"] ** 2 + c["target_im"] ** 2
+    sites = rng.choice(np.flatnonzero(weight.ravel() > 1e-3 * weight.max()), 64, replace=False)
+    g64 = trotter.Grid(c["nx"], c["ny"], "f64")
+    fd = np.zeros(len(sites))
+    h = 1e-3
+    try:
+        for i, j in enumerate(sites):
+            vals = []
+            for sgn in (1.0, -1.0):
+                V = c["V"].copy()
+                V.flat[j] += sgn * h
+                g64.set_state(c["re"], c["im"])
+                g64.set_potential(V, c["dt"], c["theta"])
+                g64.evolve_plain(c["steps"])
+                re, im = g64.get_state(np.float64)
+                vals.append(abs(np.vdot(c["target_re"] + 1j * c["target_im"], re + 1j * im)) ** 2)
+            fd[i] = (vals[0] - vals[1]) / (2 * h)
+    finally:
+        g64.close()
+    t0 = time.perf_counter()
+    og, oF, _ = oracle.adjoint_grad(c["re"], c["im"], c["target_re"], c["target_im"], c["V"],
+                                    c["dt"], c["theta"], c["steps"], nthreads=cores)
+    t_or = time.perf_counter() - t0
+    gs = grad.ravel()[sites]
+    out["c5_adjoint_1024"] = {
+        "fidelity": F, "oracle_fidelity": oF,
+        "grad_vs_fd_rel_l2": float(np.linalg.norm(gs - fd) / np.linalg.norm(fd)),
+        "grad_vs_oracle_rel_l2": float(np.linalg.norm(grad - og) / np.linalg.norm(og)),
+        "fd_sites": 64, "fd_h": h, "oracle_adjoint_s": t_or}
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_1208_2407_gb300 import trotter
@@ -766,6 +875,13 @@ def run_ours(args):
             g = None
         adjoint = adjoint_bench(args, hbm_peak)
 
+    accuracy = None
+    if rank == 0 and world == 1 and not args.no_accuracy:
+        if g is not None:
+            g.close()
+            g = None
+        accuracy = accuracy_block(args)
+
     serve = None
     if rank == 0 and not args.no_serve:
         if g is not None:
@@ -796,6 +912,7 @@ def run_ours(args):
             "precision": precision,
             "k_sweep": ksweep,
             "adjoint": adjoint,
+            "accuracy": accuracy,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)
