@@ -904,9 +904,11 @@ __device__ __forceinline__ void z_even(Frag2 &r0, Frag2 &r1, const Seg &s, const
     y_pair<PACKED>(r1.a, r1.b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
 }
 
+// The barrier of the exchange also combines the warps' `fail` flags: it
+// returns true, in every warp, if any warp of the CTA passed true.
 template <int NW>
-__device__ __forceinline__ void z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const KParams &p,
-                                      int &zbuf)
+__device__ __forceinline__ bool z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const KParams &p,
+                                      int &zbuf, bool fail)
 {
     const int lane = s.lane;
     float4 *mine = s.zx + (zbuf * NW + s.w) * 256;
@@ -918,7 +920,7 @@ __device__ __forceinline__ void z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const 
     mine[160 + lane] = r0.b.im;
     mine[192 + lane] = r1.b.re;
     mine[224 + lane] = r1.b.im;
-    __syncthreads();
+    const bool any_fail = __syncthreads_or(fail);
     const float g = p.g1, sn = p.s1;
     const float2 ng = make_float2(-g, -g), ns = make_float2(-sn, -sn), ps = make_float2(sn, sn);
     auto one = [&](Frag &f, const float4 *q, int row) {   // f <- f - g f + i s q, four columns
@@ -943,6 +945,7 @@ __device__ __forceinline__ void z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const 
         one(r1.a, q, 1);
     }
     zbuf ^= 1;
+    return any_fail;
 }
 
 // Row pair j of a segment: wait for its slots, run the pipeline, store the
@@ -966,9 +969,8 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     if constexpr (MODE == 4)   // row pair j - 2's b rows, first read now
         ok = ok && (j < 2 || wait_b<NSB>(r, j - 2, WAIT_LIMIT_NS));
     ok = __all_sync(FULL, ok);
-    // MODE 6: the CTA's warps meet at barriers, so they give up together
-    if constexpr (MODE == 6) ok = !__syncthreads_or(!ok);
-    if (!ok) {
+    // a bounded wait gave up: set the error bit, drain this warp's copies
+    auto give_up = [&]() {
         if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
         // drain this warp's outstanding copies (bounded) before leaving
         for (int jj = j, ps = r.pos_s, ph = r.par_s; jj < iss.s; ++jj) {
@@ -983,7 +985,12 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
             for (int jj = j < 2 ? 0 : j - 2; jj < iss.b; ++jj) wait_b<NSB>(r, jj, WAIT_LIMIT_NS / 4);
         }
         return false;
-    }
+    };
+    // MODE 6: the CTA's warps meet at barriers, so they give up together, at
+    // the first barrier of the row pair (the Z exchange below); until then a
+    // warp whose wait gave up computes on stale slot contents, which is
+    // harmless since nothing of it is stored
+    if (MODE != 6 && !ok) return give_up();
     const unsigned char *sj = r.ring_s + r.pos_s * C::SSLOT;
     // rows 0 and 1 of a state slot's planes (re, im) -- and (re, im) of the
     // costate in planes 2 and 3 for the backward adjoint steps
@@ -1014,20 +1021,21 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     }
     // MODE 6: a 3-D step is Ze Zo [the 2-D step] Zo Ze (Z factors commute
     // with X and Y factors): the rows entering the pipeline take Ze, Zo, the
-    // rows leaving it take Zo, Ze.  (Between row pairs the CTA meets at the
-    // barrier of the wait decision above, so each row pair may start with
-    // buffer 0.)
+    // rows leaving it take Zo, Ze.  Each row pair has two exchanges, so
+    // its first one uses buffer 0 again: the last reads of that buffer, in
+    // the previous row pair's first exchange, are behind this warp's and
+    // every other warp's second barrier since.
     int zbuf = 0;
     if constexpr (MODE == 6) {
         z_even<C::PACKED>(a, b, s, p);
-        z_odd<C::WPC>(a, b, s, p, zbuf);
+        if (z_odd<C::WPC>(a, b, s, p, zbuf, !ok)) return give_up();
     }
     const int yin = s.Ys + 2 * j;
     S O0, O1;
     pipeline_step<K, INTERIOR, MODE>(cin, cout, acc, a, b, yin, j, r.ring_p, r.pos_p, r.ring_b,
                                      r.cnt_b, s.c, p, lane, s.own, O0, O1);
     if constexpr (MODE == 6) {
-        z_odd<C::WPC>(O0, O1, s, p, zbuf);
+        z_odd<C::WPC>(O0, O1, s, p, zbuf, false);
         z_even<C::PACKED>(O0, O1, s, p);
     }
     const int yo = yin - 2 * K;
