@@ -1430,12 +1430,24 @@ cudaError_t launch3_k(const FusedLaunch &a, int nz, cudaStream_t st)
     p.n_strips = (a.nx + C::VALID - 1) / C::VALID;
     p.n_pairs = (a.ny + 1) / 2;
     p.n_zblocks = (nz + VZ - 1) / VZ;
-    // enough row ranges for about four units per resident CTA, each range at
-    // least 16 row pairs long (its pipeline fill is 2 row pairs)
+    // Row ranges per slab: the resident CTAs take the units round robin, so
+    // the launch lasts ceil(units / ctas) units while the work is units; a
+    // range of q row pairs also loads 2 more for its pipeline fill.  Take the
+    // count that keeps the most of the time useful, units / (ceil(units /
+    // ctas) ctas) * q / (q + 2), over ranges of at least 8 row pairs.
     const int64_t ctas = (int64_t)occ.num_sms * occ.blocks_per_sm;
     const int64_t blocks = (int64_t)p.n_strips * p.n_zblocks;
-    int64_t ranges = (4 * ctas + blocks - 1) / blocks;
-    ranges = std::max<int64_t>(1, std::min<int64_t>(ranges, p.n_pairs / 16));
+    int64_t ranges = 1;
+    double best = -1.0;
+    for (int64_t r = 1; r <= std::max<int64_t>(1, p.n_pairs / 8); ++r) {
+        const int64_t units = blocks * r, waves = (units + ctas - 1) / ctas;
+        const double q = (double)p.n_pairs / (double)r;
+        const double eff = (double)units / (double)(waves * ctas) * q / (q + 2.0);
+        if (eff > best) {
+            best = eff;
+            ranges = r;
+        }
+    }
     p.n_ranges = (int)ranges;
     p.units = blocks * ranges;
     p.strip_warps = 0;
