@@ -79,10 +79,11 @@ ts_status ts_grid_layout(int64_t nx, int64_t ny, ts_dtype dtype, ts_layout *out)
  * array is at (z*ny + y)*nx + x; every call that takes or returns dense
  * arrays (state, V) then uses nx*ny*nz elements.  One step applies X-even,
  * X-odd, Y-even, Y-odd, Z-even, Z-odd, exp(-i V dt), then the mirror order.
- * ts_evolve runs, for FP32 grids with even ny < 2^16 and |theta| <= pi/4,
- * a streaming Z pass and the fused 2-D step (depth 1, Y pairs kept inside
- * each slab) in turn: n steps take 2n + 1 passes over HBM (K is ignored);
- * otherwise, and for ts_evolve_plain, one kernel per sweep.  ts_observe adds
+ * ts_evolve runs, for FP32 grids with |theta| <= pi/4, one fused launch and
+ * one pass over HBM per step (the slabs' rows take the Z sweeps as they
+ * enter and leave the 2-D step, traded between neighbouring slabs; K is
+ * ignored); otherwise, and for ts_evolve_plain, one kernel per sweep.
+ * ts_observe adds
  * <z>, <z^2> and the z bonds.  3-D grids take order 2 only, no drive, no
  * adjoint, and ts_evolve_batched evolves them one by one.  Errors: as for
  * 2-D, and TS_ERR_ARG if ny * nz > 2^30. */
