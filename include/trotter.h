@@ -83,10 +83,9 @@ ts_status ts_grid_layout(int64_t nx, int64_t ny, ts_dtype dtype, ts_layout *out)
  * one pass over HBM per step (the slabs' rows take the Z sweeps as they
  * enter and leave the 2-D step, traded between neighbouring slabs; K is
  * ignored); otherwise, and for ts_evolve_plain, one kernel per sweep.
- * ts_observe adds
- * <z>, <z^2> and the z bonds.  3-D grids take order 2 only, no drive, no
- * adjoint, and ts_evolve_batched evolves them one by one.  Errors: as for
- * 2-D, and TS_ERR_ARG if ny * nz > 2^30. */
+ * ts_observe adds <z>, <z^2> and the z bonds.  3-D grids take order 2 only,
+ * no drive, no adjoint, and ts_evolve_batched evolves them one by one.
+ * Errors: as for 2-D, and TS_ERR_ARG if ny * nz > 2^30. */
 ts_status ts_grid_layout3(int64_t nx, int64_t ny, int64_t nz, ts_dtype dtype, ts_layout *out);
 ts_status ts_create_grid3(int64_t nx, int64_t ny, int64_t nz, ts_dtype dtype, void *slab,
                           size_t slab_bytes, ts_grid **out);
