@@ -241,13 +241,11 @@ ts_status ts_adjoint_backward_depth(ts_grid *g, void *ws, size_t ws_bytes, int K
     const int nx = (int)g->L.nx, ny = (int)g->L.ny;
     const int64_t pitch = g->L.pitch;
 
-    // the two quads (psi, lambda) and, for the backward launches' L2
-    // prefetches, the four G planes
-    CUtensorMap tmQ[2], tmG;
+    // the two quads (psi, lambda)
+    CUtensorMap tmQ[2];
     const char *why = "";
     if (!ts::make_pair_tensor_map(&tmQ[0], plane(WS_QA), nx, ny, pitch, PB, &why, 4) ||
-        !ts::make_pair_tensor_map(&tmQ[1], plane(WS_QB), nx, ny, pitch, PB, &why, 4) ||
-        !ts::make_pair_tensor_map(&tmG, plane(WS_G), nx, ny, pitch, PB, &why, 4))
+        !ts::make_pair_tensor_map(&tmQ[1], plane(WS_QB), nx, ny, pitch, PB, &why, 4))
         return err(TS_ERR_CUDA, "ts_adjoint_backward: %s", why);
 
     // lambda_T = phi (in quad A), G = 0
@@ -258,7 +256,6 @@ ts_status ts_adjoint_backward_depth(ts_grid *g, void *ws, size_t ws_bytes, int K
 
     ts::FusedLaunch bw;
     bw.tm_phase = &g->tm_phase;
-    bw.tm_x = &tmG;
     bw.nx = nx;
     bw.ny = ny;
     bw.pitch = pitch;

@@ -113,9 +113,6 @@ namespace {
 #ifndef TS_FUSED_FFMA2           // packed FP32 FMAs (__ffma2_rn): see Cfg<K>::PACKED
 #define TS_FUSED_FFMA2 1
 #endif
-#ifndef TS_FUSED_ADJ_PF          // backward adjoint steps: row pairs of G prefetched into
-#define TS_FUSED_ADJ_PF 2        // L2 ahead of their plain loads (0: none)
-#endif
 #ifndef TS_FUSED_DRIVE_WARP_BRANCH   // drive phase: pick the short or the reduced series
 #define TS_FUSED_DRIVE_WARP_BRANCH 1     // per warp (1) or per lane (0)
 #endif
@@ -274,16 +271,6 @@ __device__ __forceinline__ void tma_load_pair(void *dst, const CUtensorMap *tm, 
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
         "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(0), "r"(smem_addr(bar))
         : "memory");
-}
-
-// Bring one box (x in [x, x+128), rows y, y+1, planes from z) into L2 without
-// waiting for it: the plain loads that read those rows later hit in L2.
-__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap *tm, int x, int y, int z)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
-                     reinterpret_cast<uint64_t>(tm)),
-                 "r"(x), "r"(y), "r"(z)
-                 : "memory");
 }
 
 // ---- register-level sweeps ------------------------------------------------
@@ -823,7 +810,7 @@ __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int wa
 // outstanding copies are drained).
 // Per-segment constants of one warp.
 struct Seg {
-    const CUtensorMap *tm_state, *tm_phase, *tm_b, *tm_x;   // MODE 5: tm_x the G planes
+    const CUtensorMap *tm_state, *tm_phase, *tm_b;
     int XL, xg, Y0, Y1, Ys, n_iter, lane;
     int ytma;                // added to row coordinates of TMA copies (MODE 6: z ny)
     int yslab;               // MODE 6: rows from slab z to slab z + 1
@@ -1066,13 +1053,6 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
             if (more_b) issue_b<NSB>(r, s, jb);   // the slot row pair j - 3 leaves
         }
     }
-    if constexpr (MODE == 5 && TS_FUSED_ADJ_PF > 0) {
-        // into L2 ahead of their plain loads: the G rows that the last step
-        // adds into TS_FUSED_ADJ_PF iterations from now (row pair j + PF - K + 1)
-        const int q = j + TS_FUSED_ADJ_PF - K + 1, y = s.Ys + 2 * q;
-        if (lane == 0 && q >= 0 && q < s.n_iter && y >= 0 && y < p.ny)
-            tma_prefetch_l2(s.tm_x, s.XL, y, 0);
-    }
     iss.s += more_s;
     iss.p += more_p;
     iss.b += more_b;
@@ -1087,7 +1067,7 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
 template <int K, int MODE>
 __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_state,
                                             const CUtensorMap *tm_phase, const CUtensorMap *tm_b,
-                                            const CUtensorMap *tm_x, const KParams &p, int sx,
+                                            const KParams &p, int sx,
                                             int q0, int q1, int lane, const Slab3 &sl = Slab3())
 {
     using C = CfgM<K, MODE>;
@@ -1098,7 +1078,6 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     s.tm_state = tm_state;
     s.tm_phase = tm_phase;
     s.tm_b = tm_b;
-    s.tm_x = tm_x;
     s.ytma = sl.ytma;
     s.yslab = p.ny;
     s.z = sl.z;
@@ -1204,7 +1183,7 @@ __global__ void __launch_bounds__(Cfg<K>::WPC * 32, min_blocks(K, MODE))
 fused_kernel(const __grid_constant__ CUtensorMap tm_state,
              const __grid_constant__ CUtensorMap tm_phase,
              const __grid_constant__ CUtensorMap tm_b,
-             const __grid_constant__ CUtensorMap tm_x, const KParams p)
+             const KParams p)
 {
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1218,7 +1197,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
         const int sx = gw / p.strip_warps, i = gw - sx * p.strip_warps;
         const int q0 = (int)((int64_t)i * p.n_pairs / p.strip_warps);
         const int q1 = (int)((int64_t)(i + 1) * p.n_pairs / p.strip_warps);
-        if (q1 > q0) run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, &tm_x, p, sx, q0, q1, lane);
+        if (q1 > q0) run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, p, sx, q0, q1, lane);
         return;
     }
     const int64_t u_begin = (int64_t)gw * p.units / p.total_warps;
@@ -1229,7 +1208,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tm_state,
         const int64_t q1_want = (int64_t)q0 + (u_end - u);
         const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
         u += q1 - q0;
-        if (!run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, &tm_x, p, sx, q0, q1, lane)) return;
+        if (!run_segment<K, MODE>(r, &tm_state, &tm_phase, &tm_b, p, sx, q0, q1, lane)) return;
     }
 }
 
@@ -1286,7 +1265,7 @@ fused3d_kernel(const __grid_constant__ CUtensorMap tm_state,
             pw.out2_re = p.out_re + (sl.z + 1) * slab;
             pw.out2_im = p.out_im + (sl.z + 1) * slab;
         }
-        if (!run_segment<K, 6>(r, &tm_state, &tm_phase, nullptr, nullptr, pw, sx, q0, q1, lane, sl))
+        if (!run_segment<K, 6>(r, &tm_state, &tm_phase, nullptr, pw, sx, q0, q1, lane, sl))
             return;
     }
 }
@@ -1355,7 +1334,7 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
         const int q0 = (int)((int64_t)i * p.n_pairs / w);
         const int q1 = (int)((int64_t)(i + 1) * p.n_pairs / w);
         if (q1 > q0)
-            run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, nullptr, p, sx, q0, q1, lane);
+            run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, p, sx, q0, q1, lane);
         return;
     }
     const int64_t u_begin = (int64_t)gw * total_units / total_warps;
@@ -1385,7 +1364,7 @@ fused_multi_kernel(const EpochEntry *__restrict__ tab, int n_grids, int64_t tota
         if (q1_want > q0 + left_in_grid) q1_want = q0 + left_in_grid;
         const int q1 = (int)(q1_want < p.n_pairs ? q1_want : (int64_t)p.n_pairs);
         u += q1 - q0;
-        if (!run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, nullptr, p, sx, q0, q1, lane)) return;
+        if (!run_segment<K, 0>(r, &d->tm_state[cur], &d->tm_phase, nullptr, p, sx, q0, q1, lane)) return;
     }
 }
 
@@ -1527,8 +1506,7 @@ cudaError_t launch_k(const FusedLaunch &a, cudaStream_t st)
     p.sab = a.sab;
     const int blocks = (p.total_warps + C::WPC - 1) / C::WPC;
     fused_kernel<K, MODE><<<blocks, C::WPC * 32, C::SMEM, st>>>(
-        *a.tm_state, *a.tm_phase, a.tm_b ? *a.tm_b : *a.tm_phase,
-        a.tm_x ? *a.tm_x : *a.tm_phase, p);
+        *a.tm_state, *a.tm_phase, a.tm_b ? *a.tm_b : *a.tm_phase, p);
     count_launches(1);
     return cudaGetLastError();
 }

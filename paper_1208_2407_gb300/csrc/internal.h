@@ -87,7 +87,6 @@ struct FusedLaunch {
     const CUtensorMap *tm_state;   // (re, im) planes of the input pair, 3-D map
     const CUtensorMap *tm_phase;   // (gamma_V, s_V) planes, 3-D map
     const CUtensorMap *tm_b = nullptr;   // launch_fused_u4: the b substep's table
-    const CUtensorMap *tm_x = nullptr;   // launch_fused_adjoint: the 4 G planes
     float *out_re, *out_im;
     int nx, ny;
     int64_t pitch;
@@ -115,8 +114,7 @@ cudaError_t launch_fused(int K, const FusedLaunch &a, cudaStream_t st);
 // coefficients at -theta) on two states at once: tm_state maps four planes
 // (psi re, im, lambda re, im), psi goes to (out_re, out_im) and lambda to
 // (out2_re, out2_im).  At each step's phase point G += conj(lambda~) m, with
-// lambda~ = B^dagger lambda_s and m = B^dagger psi_s; tm_x maps G's four
-// planes (for L2 prefetches of the rows about to be added into).
+// lambda~ = B^dagger lambda_s and m = B^dagger psi_s.
 constexpr int FUSED_ADJ_MAX_K = 4;
 cudaError_t launch_fused_adjoint(int K, const FusedLaunch &a, cudaStream_t st);
 // K (1..4) steps with the time-dependent potential V0 + a_n V1: tm_phase
