@@ -412,24 +412,19 @@ __device__ __forceinline__ void phase4(Frag2 &f, float4 g, float4 s)
 // potential): adt = a_n dt of the step, v1 = the row's V1 values, so the
 // angle of a site is phi = adt V1.  With u = phi^2, sin(phi) = phi P(u) and
 // 1 - cos(phi) = u Q(u), P and Q the Taylor series of sin(x)/x and
-// (1 - cos x)/x^2 in u through u^N: N = 3 keeps the truncation under 1.2e-8
-// for |phi| <= 0.5, N = 4 under 3e-9 for |phi| <= 0.8 (an FP32 emulation of
-// this evaluation gives relative errors under 1.5e-7 in both).
-template <int N>
+// (1 - cos x)/x^2 in u through u^4: the truncation stays under 3e-9 for
+// |phi| <= 0.8, and an FP32 emulation of this evaluation gives relative
+// errors under 1.5e-7.  (A second, shorter series for smaller angles
+// measured slower: the kernel is bound by instruction issue and
+// instruction-cache misses, not by these operations.)
 __device__ __forceinline__ void versine_phi2(float2 phi, float2 &g, float2 &s)
 {
     auto c2 = [](float v) { return make_float2(v, v); };
     const float2 u = __fmul2_rn(phi, phi);
-    float2 P, Q;
-    if constexpr (N == 4) {
-        P = __ffma2_rn(u, c2(1.0f / 362880.0f), c2(-1.0f / 5040.0f));
-        Q = __ffma2_rn(u, c2(1.0f / 3628800.0f), c2(-1.0f / 40320.0f));
-        P = __ffma2_rn(u, P, c2(1.0f / 120.0f));
-        Q = __ffma2_rn(u, Q, c2(1.0f / 720.0f));
-    } else {
-        P = __ffma2_rn(u, c2(-1.0f / 5040.0f), c2(1.0f / 120.0f));
-        Q = __ffma2_rn(u, c2(-1.0f / 40320.0f), c2(1.0f / 720.0f));
-    }
+    float2 P = __ffma2_rn(u, c2(1.0f / 362880.0f), c2(-1.0f / 5040.0f));
+    float2 Q = __ffma2_rn(u, c2(1.0f / 3628800.0f), c2(-1.0f / 40320.0f));
+    P = __ffma2_rn(u, P, c2(1.0f / 120.0f));
+    Q = __ffma2_rn(u, Q, c2(1.0f / 720.0f));
     P = __ffma2_rn(u, P, c2(-1.0f / 6.0f));
     Q = __ffma2_rn(u, Q, c2(-1.0f / 24.0f));
     P = __ffma2_rn(u, P, c2(1.0f));
@@ -439,20 +434,13 @@ __device__ __forceinline__ void versine_phi2(float2 phi, float2 &g, float2 &s)
 }
 
 // The same on one column (same operations, same rounding).
-template <int N>
 __device__ __forceinline__ void versine_phi(float phi, float &g, float &s)
 {
     const float u = phi * phi;
-    float P, Q;
-    if constexpr (N == 4) {
-        P = fmaf(u, 1.0f / 362880.0f, -1.0f / 5040.0f);
-        Q = fmaf(u, 1.0f / 3628800.0f, -1.0f / 40320.0f);
-        P = fmaf(u, P, 1.0f / 120.0f);
-        Q = fmaf(u, Q, 1.0f / 720.0f);
-    } else {
-        P = fmaf(u, -1.0f / 5040.0f, 1.0f / 120.0f);
-        Q = fmaf(u, -1.0f / 40320.0f, 1.0f / 720.0f);
-    }
+    float P = fmaf(u, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    float Q = fmaf(u, 1.0f / 3628800.0f, -1.0f / 40320.0f);
+    P = fmaf(u, P, 1.0f / 120.0f);
+    Q = fmaf(u, Q, 1.0f / 720.0f);
     P = fmaf(u, P, -1.0f / 6.0f);
     Q = fmaf(u, Q, -1.0f / 24.0f);
     P = fmaf(u, P, 1.0f);
@@ -461,38 +449,36 @@ __device__ __forceinline__ void versine_phi(float phi, float &g, float &s)
     g = u * Q;
 }
 
-template <int N, bool PACKED>
+template <bool PACKED>
 __device__ __forceinline__ void versine_phi4(float4 phi, float4 &g, float4 &s)
 {
     if constexpr (PACKED) {
         float2 g0, s0, g1, s1;
-        versine_phi2<N>(lo2(phi), g0, s0);
-        versine_phi2<N>(hi2(phi), g1, s1);
+        versine_phi2(lo2(phi), g0, s0);
+        versine_phi2(hi2(phi), g1, s1);
         g = join2(g0, g1);
         s = join2(s0, s1);
     } else {
-        versine_phi<N>(phi.x, g.x, s.x);
-        versine_phi<N>(phi.y, g.y, s.y);
-        versine_phi<N>(phi.z, g.z, s.z);
-        versine_phi<N>(phi.w, g.w, s.w);
+        versine_phi(phi.x, g.x, s.x);
+        versine_phi(phi.y, g.y, s.y);
+        versine_phi(phi.z, g.z, s.z);
+        versine_phi(phi.w, g.w, s.w);
     }
 }
 
 template <bool PACKED>
 __device__ __forceinline__ void drive4(Frag &f, float4 v1, float adt)
 {
-    // the angles of the lane's four columns; the series of the smallest
-    // degree that serves every lane of the warp is taken, so that the branch
-    // does not diverge (all lanes are converged here); angles beyond 0.8
-    // take the reduced path, on the half angle
+    // the angles of the lane's four columns; the series serves when every
+    // angle in the warp is at most 0.8 -- decided for the whole warp, so that
+    // the branch does not diverge (all lanes are converged here); larger
+    // angles take the reduced path, on the half angle
     const float4 phi = make_float4(adt * v1.x, adt * v1.y, adt * v1.z, adt * v1.w);
     float4 g, s;
     const float m = fmaxf(fmaxf(fabsf(phi.x), fabsf(phi.y)), fmaxf(fabsf(phi.z), fabsf(phi.w)));
     auto all = [](bool b) { return TS_FUSED_DRIVE_WARP_BRANCH ? __all_sync(FULL, b) : b; };
-    if (all(m <= 0.5f)) {
-        versine_phi4<3, PACKED>(phi, g, s);
-    } else if (all(m <= 0.8f)) {
-        versine_phi4<4, PACKED>(phi, g, s);
+    if (all(m <= 0.8f)) {
+        versine_phi4<PACKED>(phi, g, s);
     } else {
         const float4 h = make_float4(0.5f * phi.x, 0.5f * phi.y, 0.5f * phi.z, 0.5f * phi.w);
         versine_reduced(h.x, g.x, s.x);

@@ -213,9 +213,9 @@ def test_uniform_force_drift_closed_form_on_the_gpu():
 def test_drive_phase_alone_against_closed_form(scale):
     """theta = 0 and V0 = 0 leave only the drive phases: psi_T = psi_0
     exp(-i dt V1 sum_n a_n) per site.  Angles from 1e-5 to ~1e4 rad per step
-    cover both series (angles up to 0.5 and up to 0.8: scale 10 puts warps in
-    the second) and the reduced path; the per-site error bound is about 1e-6
-    per step (series, reduction and the phase update in FP32)."""
+    cover the series (angles up to 0.8: scale 10 puts warps near that edge)
+    and the reduced path; the per-site error bound is about 1e-6 per step
+    (series, reduction and the phase update in FP32)."""
     rng = np.random.default_rng(16)
     nx, ny, steps, dt = 160, 40, 8, 0.05
     re, im = random_state(rng, nx, ny)
