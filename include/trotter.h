@@ -268,7 +268,7 @@ ts_status ts_evolve_batched(ts_grid *const *g, int n, const int64_t *steps, int 
  * ts_adjoint_backward: after a forward with the same ws, writes dF/dV as a
  *   dense nx*ny FP32 device array `grad`.  Syncs.  One forward/backward pair
  *   per grid at a time; TS_ERR_STATE without a matching forward.
- *   psi and lambda step back together, K steps per fused launch (K = 2).
+ *   psi and lambda step back together, K steps per fused launch (K = 3).
  * ts_adjoint_backward_depth: the same with the depth K of those launches
  *   given (1..4; 0 = the default); other K return TS_ERR_ARG.  K changes only
  *   the order in which G's terms are summed, not the gradient it defines.

@@ -36,8 +36,8 @@
 #include "internal.h"
 #include "trace.h"
 
-#ifndef TS_ADJ_DEFAULT_K      // fused depth of the recomputation and backward launches
-#define TS_ADJ_DEFAULT_K 2
+#ifndef TS_ADJ_DEFAULT_K      // fused depth of the backward launches
+#define TS_ADJ_DEFAULT_K 3
 #endif
 
 namespace {

@@ -120,8 +120,8 @@ namespace {
 #define TS_FUSED3D_WARPS 8       // first and last warp hold halo slabs
 #endif
 #ifndef TS_FUSED_PF_DUAL         // row pairs prefetched ahead of use by the backward
-#define TS_FUSED_PF_DUAL 2       // adjoint steps (two states per slot)
-#endif
+#define TS_FUSED_PF_DUAL 1       // adjoint steps (two states per slot); one row pair
+#endif                           // ahead leaves room for 8 warps per SM at depth 3
 constexpr int PLANE_SLOT_BYTES = FUSED_BOX_ROWS * FUSED_BOX_COLS * 4;   // 1 KiB
 constexpr int SLOT_BYTES = 2 * PLANE_SLOT_BYTES;     // one ring slot: two planes of 2 rows
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;    // 2 s per wait
@@ -149,8 +149,8 @@ __host__ __device__ constexpr int phase_planes(int mode)
 __host__ __device__ constexpr int state_planes(int mode) { return mode == 5 || mode == 6 ? 4 : 2; }
 
 // __launch_bounds__ minimum resident blocks of the single-grid kernel; the
-// backward adjoint steps (MODE 5) carry two states and K - 1 running sums of
-// G's terms, and are not held to the forward depth's occupancy
+// backward adjoint steps (MODE 5) carry two states and are not held to the
+// forward depth's occupancy
 __host__ __device__ constexpr int min_blocks(int K, int MODE = 0)
 {
     return MODE == 5   ? TS_FUSED_MIN_BLOCKS
@@ -178,7 +178,12 @@ struct Cfg {
                               : K == 1 ? TS_FUSED_PF_K1
                               : K == 2 ? TS_FUSED_PF_K2
                                        : TS_FUSED_PF_DEEP;
-    static constexpr bool PINGPONG = K >= TS_FUSED_PINGPONG_MIN_K && K <= TS_FUSED_PINGPONG_MAX_K;
+    static constexpr bool PINGPONG = M != 5 && K >= TS_FUSED_PINGPONG_MIN_K && K <= TS_FUSED_PINGPONG_MAX_K;
+    // The backward adjoint steps carry two states: one carry set, which
+    // leaves registers for the deeper pipelines, and interior row pairs one
+    // per loop trip instead of two, a smaller loop body (2-3 % faster for
+    // them; about 1 % slower for one state and for the 3-D steps).
+    static constexpr bool ONE_PAIR = M == 5;
     // packed FP32 FMAs in the Y sweeps and the phase: 0 never, 1 for every
     // depth but 2 (where the scalar form measured faster), 2 always
     static constexpr bool PACKED = TS_FUSED_FFMA2 == 2 || (TS_FUSED_FFMA2 == 1 && K != 2);
@@ -193,7 +198,13 @@ struct Cfg {
     static constexpr int NSB = BRING ? PF + 2 : 0;
     static constexpr int NBAR = NSS + NSP + NSB;   // mbarriers per warp
     static constexpr int SSLOT = SP * PLANE_SLOT_BYTES;   // a state slot
-    static constexpr int WARP_SMEM = NSS * SSLOT + NSP * PSLOT + NSB * SLOT_BYTES;
+    // MODE 5: the running sums of G's terms of the row pairs in flight, two
+    // rows for each of the steps 0 .. K - 2, [slot][re, im][lane] as float4
+    static constexpr int SUMS_BYTES = M == 5 ? 2 * (K - 1) * 1024 : 0;
+    // MODE 5: G's rows for the next commit, staged by cp.async (two rows of
+    // four planes, [row][plane][lane] as float4)
+    static constexpr int GST_BYTES = M == 5 ? 4096 : 0;
+    static constexpr int WARP_SMEM = NSS * SSLOT + NSP * PSLOT + NSB * SLOT_BYTES + SUMS_BYTES + GST_BYTES;
     // MODE 6: two buffers through which the CTA's warps trade their rows for
     // the odd Z sweeps (a row pair of re, im of both slabs per warp: 4 KiB)
     static constexpr int ZX_BYTES = M == 6 ? 2 * WPC * 4 * PLANE_SLOT_BYTES : 0;
@@ -527,6 +538,8 @@ struct Owned {
     int Y0, Y1;        // output rows [Y0, Y1)
     int xg;            // the lane's first column
     bool lane_ok;      // the lane's 4 columns are inside the valid strip and < nx
+    float4 *sums;      // MODE 5: the lane's running sums (shared memory)
+    float4 *gst;       // MODE 5: the lane's staged G rows (shared memory)
 };
 
 __device__ __forceinline__ bool owns_row(const Owned &w, const KParams &p, int row)
@@ -559,15 +572,46 @@ __device__ __forceinline__ Frag frag_add(const Frag &a, const Frag &b)
     return r;
 }
 
-// G += t for one owned row, in double-float (hi + lo planes)
-__device__ __forceinline__ void adj_commit(const Frag &t, int row, const Owned &w,
+// G's rows are staged in shared memory by cp.async one iteration before the
+// terms are added to them, so their loads overlap the iteration's sweeps
+// (plain loads at the commit left the kernel waiting on them).  Each lane
+// copies its own 16 bytes of each plane and reads back only those, so the
+// lane's own wait orders the accesses.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// stage slot `slot` (0 or 1) of the lane: [plane rh, rl, ih, il][lane]
+__device__ __forceinline__ void adj_stage(int row, int slot, const Owned &w, const KParams &p)
+{
+    const int64_t o = (int64_t)row * p.pitch + w.xg;
+    float4 *st = w.gst + slot * 128;
+    cp_async16(st, p.g_rh + o);
+    cp_async16(st + 32, p.g_rl + o);
+    cp_async16(st + 64, p.g_ih + o);
+    cp_async16(st + 96, p.g_il + o);
+}
+
+// G += t for one owned row, in double-float (hi + lo planes, Knuth's
+// two-sum), from its staged values
+__device__ __forceinline__ void adj_commit(const Frag &t, int row, int slot, const Owned &w,
                                            const KParams &p)
 {
     const int64_t o = (int64_t)row * p.pitch + w.xg;
-    float4 rh = *reinterpret_cast<const float4 *>(p.g_rh + o);
-    float4 rl = *reinterpret_cast<const float4 *>(p.g_rl + o);
-    float4 ih = *reinterpret_cast<const float4 *>(p.g_ih + o);
-    float4 il = *reinterpret_cast<const float4 *>(p.g_il + o);
+    const float4 *st = w.gst + slot * 128;
+    float4 rh = st[0], rl = st[32], ih = st[64], il = st[96];
     auto acc = [](float &hi, float &lo, float v) {
         FF s = two_sum(hi, v);
         s.lo += lo;
@@ -591,15 +635,16 @@ __device__ __forceinline__ void adj_commit(const Frag &t, int row, const Owned &
 
 // MODE 5 at the phase point of step k of the launch, rows (y1, y1 + 1) held
 // in (P, Q) (psi in .a, lambda in .b).  The pair reached step k here one
-// iteration after it reached step k - 1, so its running sum is carried in
-// registers: acc[2k], acc[2k+1] hold, between iterations, the sum of the
-// pair that is at step k now; car passes the sum of step k - 1 from the
-// previous iteration to this step.  Step K - 1 adds the finished sum into G
-// (owned rows only; other rows' sums are never stored).
+// iteration after it reached step k - 1, so its running sum waits in shared
+// memory between iterations: sum slots 2k and 2k + 1 hold the sum of the pair
+// that is at step k now; car passes the sum of step k - 1 from the previous
+// iteration to this step.  Step K - 1 adds the finished sum into G (owned
+// rows only; other rows' sums are never stored).  Each lane touches only its
+// own entries, so no synchronisation is needed.
 template <int K>
 __device__ __forceinline__ void adj_step(int k, const Frag2 &P, const Frag2 &Q, int y1,
-                                         Frag (&acc)[2 * K], Frag &carP, Frag &carQ,
-                                         const Owned &w, const KParams &p)
+                                         Frag &carP, Frag &carQ, const Owned &w,
+                                         const KParams &p)
 {
     Frag tP = adj_term(P.b, P.a), tQ = adj_term(Q.b, Q.a);
     if (k > 0) {
@@ -607,13 +652,24 @@ __device__ __forceinline__ void adj_step(int k, const Frag2 &P, const Frag2 &Q, 
         tQ = frag_add(carQ, tQ);
     }
     if (k == K - 1) {
-        if (owns_row(w, p, y1)) adj_commit(tP, y1, w, p);
-        if (owns_row(w, p, y1 + 1)) adj_commit(tQ, y1 + 1, w, p);
+        // rows (y1, y1 + 1) were staged by the previous iteration, which
+        // committed (y1 - 2, y1 - 1); stage the next iteration's rows
+        cp_async_wait_all();
+        if (owns_row(w, p, y1)) adj_commit(tP, y1, 0, w, p);
+        if (owns_row(w, p, y1 + 1)) adj_commit(tQ, y1 + 1, 1, w, p);
+        if (owns_row(w, p, y1 + 2)) adj_stage(y1 + 2, 0, w, p);
+        if (owns_row(w, p, y1 + 3)) adj_stage(y1 + 3, 1, w, p);
+        cp_async_commit();
     } else {
-        carP = acc[2 * k];
-        carQ = acc[2 * k + 1];
-        acc[2 * k] = tP;
-        acc[2 * k + 1] = tQ;
+        float4 *a0 = w.sums + 2 * k * 64, *a1 = a0 + 64;
+        carP.re = a0[0];
+        carP.im = a0[32];
+        carQ.re = a1[0];
+        carQ.im = a1[32];
+        a0[0] = tP.re;
+        a0[32] = tP.im;
+        a1[0] = tQ.re;
+        a1[32] = tQ.im;
     }
 }
 
@@ -627,11 +683,11 @@ __device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y
 // time-dependent potential; MODE 4: one fourth-order step; MODE 5: backward
 // adjoint steps U^dagger on two states (the caller passes the coefficients at
 // -theta; the phase is conjugated here) that accumulate G at each step's
-// phase point, with the running sums of the rows in flight carried in `acc`
+// phase point, with the running sums of the rows in flight in shared memory
 // (updated in place).
 template <int K, bool INTERIOR, int MODE, typename S = StateT<MODE>>
 __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2 * K],
-                                              Frag (&acc)[2 * K], S a, S b, int yin, int j,
+                                              S a, S b, int yin, int j,
                                               const unsigned char *ring_p, int pos_p,
                                               const unsigned char *ring_b, int cnt_b,
                                               const StripCoef &c, const KParams &p, int lane,
@@ -671,7 +727,7 @@ __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2
     cout[0] = b;
     int y1 = yin - 1;
     Frag carP, carQ;   // MODE 5: running sums handed from step k - 1 to step k
-    if constexpr (MODE == 5) adj_step<K>(0, P, Q, y1, acc, carP, carQ, w, p);
+    if constexpr (MODE == 5) adj_step<K>(0, P, Q, y1, carP, carQ, w, p);
     // the phase of step k on one row from phase slot sp (row 0 or 1 of the
     // slot): conjugated in a backward step (exp(+i V dt) has sine -s_V); with
     // the drive term for MODE 3; MODE 6 holds two slabs, each with its table
@@ -723,7 +779,7 @@ __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2
         cout[2 * k] = Q2;
         Q = P2;
         y1 -= 2;
-        if constexpr (MODE == 5) adj_step<K>(k, P, Q, y1, acc, carP, carQ, w, p);
+        if constexpr (MODE == 5) adj_step<K>(k, P, Q, y1, carP, carQ, w, p);
         // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
         // (MODE 4: the b substep's table comes from the b ring; MODE 5: the
         // conjugate phase, sine -s_V)
@@ -755,6 +811,7 @@ __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2
 struct WarpRings {
     uint64_t *bar_s, *bar_p, *bar_b;
     unsigned char *ring_s, *ring_p, *ring_b;
+    float4 *sums, *gst;   // MODE 5: running sums, staged G rows (this lane's)
     int pos_s, pos_p;
     uint32_t par_s, par_p;
     // b ring: b copies are numbered across the warp's segments; copy L sits
@@ -779,6 +836,8 @@ __device__ __forceinline__ WarpRings carve_rings(unsigned char *smem_raw, int wa
     r.ring_s = smem_raw + slots_off + (size_t)warp * C::WARP_SMEM;
     r.ring_p = r.ring_s + NSS * C::SSLOT;
     r.ring_b = r.ring_p + NSP * C::PSLOT;
+    r.sums = reinterpret_cast<float4 *>(r.ring_b + C::NSB * SLOT_BYTES) + lane;
+    r.gst = reinterpret_cast<float4 *>(r.ring_b + C::NSB * SLOT_BYTES + C::SUMS_BYTES) + lane;
     r.pos_s = r.pos_p = 0;
     r.par_s = r.par_p = 0;
     r.cnt_b = 0;
@@ -932,7 +991,7 @@ struct Issued {
 template <int K, int MODE, bool INTERIOR, typename S = StateT<MODE>>
 __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KParams &p, int j,
                                          const S (&cin)[2 * K], S (&cout)[2 * K],
-                                         Frag (&acc)[2 * K], Issued &iss)
+                                         Issued &iss)
 {
     using C = CfgM<K, MODE>;
     constexpr int NSS = C::NSS, NSP = C::NSP, NSB = C::NSB;
@@ -945,6 +1004,7 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     // a bounded wait gave up: set the error bit, drain this warp's copies
     auto give_up = [&]() {
         if (lane == 0) atomicOr(p.err, ERRBIT_WAIT_TIMEOUT);
+        if constexpr (C::GST_BYTES > 0) cp_async_wait_all();
         // drain this warp's outstanding copies (bounded) before leaving
         for (int jj = j, ps = r.pos_s, ph = r.par_s; jj < iss.s; ++jj) {
             mbar_wait(&r.bar_s[ps], ph, WAIT_LIMIT_NS / 4);
@@ -1005,7 +1065,7 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     }
     const int yin = s.Ys + 2 * j;
     S O0, O1;
-    pipeline_step<K, INTERIOR, MODE>(cin, cout, acc, a, b, yin, j, r.ring_p, r.pos_p, r.ring_b,
+    pipeline_step<K, INTERIOR, MODE>(cin, cout, a, b, yin, j, r.ring_p, r.pos_p, r.ring_b,
                                      r.cnt_b, s.c, p, lane, s.own, O0, O1);
     if constexpr (MODE == 6) {
         z_odd<C::WPC>(O0, O1, s, p, zbuf, false);
@@ -1094,7 +1154,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
         s.c.Eab = {e0 ? p.tab : 0.f, e0 ? p.sab : 0.f, e1 ? p.tab : 0.f, e1 ? p.sab : 0.f};
     }
     s.store_lane = lane >= HALO / 4 && lane < 32 - HALO / 4 && xg < p.nx;
-    s.own = {s.Y0, s.Y1, xg, s.store_lane};
+    s.own = {s.Y0, s.Y1, xg, s.store_lane, r.sums, r.gst};
 
     const int n_pro_s = s.n_iter < NSS ? s.n_iter : NSS;
     const int n_pro_p = s.n_iter < NSP ? s.n_iter : NSP;
@@ -1115,34 +1175,47 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     // first reads set A and writes set B and the second goes back into A, so
     // no row is copied between iterations (at the price of registers, which
     // shallow pipelines keep for occupancy); edge row pairs update A in place.
-    // MODE 5: running sums of G's terms for the row pairs in flight (the
-    // sums of rows this warp owns start inside the segment; the rows of its
-    // first iterations are not this warp's and are never stored)
+    // MODE 5 keeps one set and takes one row pair per trip.  Its running sums
+    // of G's terms start at zero (the sums of rows this warp owns start
+    // inside the segment; the rows of its first iterations are not this
+    // warp's and are never stored)
     S cA[2 * K], cB[2 * K];
-    Frag acc[2 * K];
 #pragma unroll
-    for (int i = 0; i < 2 * K; ++i) {
-        cA[i] = zero_state<S>();
-        acc[i] = zero_frag();
+    for (int i = 0; i < 2 * K; ++i) cA[i] = zero_state<S>();
+    if constexpr (C::SUMS_BYTES > 0) {
+#pragma unroll
+        for (int i = 0; i < 2 * (K - 1); ++i) {
+            r.sums[i * 64] = make_float4(0.f, 0.f, 0.f, 0.f);
+            r.sums[i * 64 + 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
     auto interior = [&](int j) {
         const int yin = s.Ys + 2 * j;
         return j >= K && yin - 2 * K >= 0 && yin + 1 < p.ny;
     };
     for (int j = 0; j < s.n_iter;) {
+        if (C::ONE_PAIR) {
+            if (interior(j)) {
+                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cA, iss)) return false;
+            } else if (!row_pair<K, MODE, false>(r, s, p, j, cA, cA, iss)) {
+                return false;
+            }
+            j += 1;
+            continue;
+        }
         if (j + 1 < s.n_iter && interior(j) && interior(j + 1)) {
             if (C::PINGPONG) {
-                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cB, acc, iss)) return false;
-                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cB, cA, acc, iss))
+                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cB, iss)) return false;
+                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cB, cA, iss))
                     return false;
             } else {
-                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cA, acc, iss)) return false;
-                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cA, cA, acc, iss))
+                if (!row_pair<K, MODE, true>(r, s, p, j, cA, cA, iss)) return false;
+                if (!row_pair<K, MODE, true>(r, s, p, j + 1, cA, cA, iss))
                     return false;
             }
             j += 2;
         } else {
-            if (!row_pair<K, MODE, false>(r, s, p, j, cA, cA, acc, iss)) return false;
+            if (!row_pair<K, MODE, false>(r, s, p, j, cA, cA, iss)) return false;
             j += 1;
         }
     }
@@ -1158,6 +1231,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
         }
         r.cnt_b += s.n_iter;
     }
+    if constexpr (C::GST_BYTES > 0) cp_async_wait_all();
     __syncwarp();
     return true;
 }
