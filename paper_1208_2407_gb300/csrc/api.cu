@@ -799,7 +799,7 @@ ts_status fused_steps(ts_grid *g, int64_t steps, int K, cudaStream_t st)
 // neighbouring steps run back to back (a run of 2 at either end, of 4
 // between two b substeps), so on the fused path each run of r substeps is
 // ceil(r / K) launches of near-equal depth; each b substep is one launch.
-// 3-D steps on the fast path (FP32, |theta| <= pi/4, (nz + 16) ny < 2^31):
+// 3-D steps on the fast path (FP32, |theta| <= pi/4, (nz + 32) ny < 2^31):
 // one launch and one HBM round trip per step (fused.cu, fused3d_kernel).  Z
 // factors commute with X and Y factors, so the step
 //   Xe Xo Ye Yo Ze Zo P Zo Ze Yo Ye Xo Xe
@@ -967,8 +967,9 @@ ts_status ts_evolve(ts_grid *g, int64_t steps, int K, void *stream)
         return evolve_f64(g, steps, st);
     }
     if (g->is3d()) {
-        // (TMA row coordinates reach (nz + 14) ny: the last z-block's halo slabs)
-        if (std::fabs(g->theta) > 0.25 * M_PI || (g->L.nz + 16) * g->L.ny >= (int64_t(1) << 31))
+        // (TMA row coordinates reach about (nz + 2 W - 3) ny for a block of W
+        // warps, W <= 16: the last z-block's halo slabs)
+        if (std::fabs(g->theta) > 0.25 * M_PI || (g->L.nz + 32) * g->L.ny >= (int64_t(1) << 31))
             return plain_steps(g, steps, st);
         return evolve3_fused(g, steps, st);
     }

@@ -117,7 +117,7 @@ namespace {
 #define TS_FUSED_DRIVE_WARP_BRANCH 1     // per warp (1) or per lane (0)
 #endif
 #ifndef TS_FUSED3D_WARPS         // 3-D steps: warps per CTA (two slabs each); the CTA's
-#define TS_FUSED3D_WARPS 8       // first and last warp hold halo slabs
+#define TS_FUSED3D_WARPS 12      // first and last warp hold halo slabs
 #endif
 #ifndef TS_FUSED_PF_DUAL         // row pairs prefetched ahead of use by the backward
 #define TS_FUSED_PF_DUAL 1       // adjoint steps (two states per slot); one row pair
@@ -169,7 +169,7 @@ __host__ __device__ constexpr int multi_min_blocks(int K)
 
 template <int K, int PP = 2, bool BRING = false, int SP = 2, int M = 0>
 struct Cfg {
-    // MODE 6 (3-D steps): one CTA of TS_FUSED3D_WARPS warps, one slab each
+    // MODE 6 (3-D steps): one CTA of TS_FUSED3D_WARPS warps, two slabs each
     static constexpr int WPC = M == 6 ? TS_FUSED3D_WARPS
                                : K <= 2 ? TS_FUSED_WPC_SHALLOW
                                         : TS_FUSED_WPC_DEEP;
@@ -188,7 +188,11 @@ struct Cfg {
     // depth but 2 (where the scalar form measured faster), 2 always
     static constexpr bool PACKED = TS_FUSED_FFMA2 == 2 || (TS_FUSED_FFMA2 == 1 && K != 2);
     static constexpr int NSS = PF + 1;
-    static constexpr int NSP = PF + K + 1;
+    // phase ring: step k of iteration j reads the rows of pair j - k and of
+    // pair j - k - 1, so the ring holds K + 1 pairs and the PF ahead; MODE 6
+    // loads each slot one row earlier (rows 2j - 1 and 2j of the pair's
+    // range), which puts both rows of a step in one slot
+    static constexpr int NSP = PF + K + (M == 6 ? 0 : 1);
     static constexpr int HALO = ((2 * K + 3) / 4) * 4;
     static constexpr int VALID = FUSED_BOX_COLS - 2 * HALO;
     // a phase slot holds (gamma_V, s_V) and, with a drive, the V1 rows too
@@ -205,10 +209,7 @@ struct Cfg {
     // four planes, [row][plane][lane] as float4)
     static constexpr int GST_BYTES = M == 5 ? 4096 : 0;
     static constexpr int WARP_SMEM = NSS * SSLOT + NSP * PSLOT + NSB * SLOT_BYTES + SUMS_BYTES + GST_BYTES;
-    // MODE 6: two buffers through which the CTA's warps trade their rows for
-    // the odd Z sweeps (a row pair of re, im of both slabs per warp: 4 KiB)
-    static constexpr int ZX_BYTES = M == 6 ? 2 * WPC * 4 * PLANE_SLOT_BYTES : 0;
-    static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + NBAR * 8) + ZX_BYTES;
+    static constexpr int SMEM = 1024 + WPC * (WARP_SMEM + NBAR * 8);
 };
 
 // The configuration of a mode's kernel at depth K.
@@ -742,8 +743,14 @@ __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2
         }
     };
     // phase of step 0 on rows (y1, y1+1): slot j-1 row 1, slot j row 0
-    if (INTERIOR || j >= 1) phase_row(P, slot_p(1), 1, 0);
-    phase_row(Q, slot_p(0), 0, 0);
+    // (MODE 6: rows 0 and 1 of slot j)
+    if constexpr (MODE == 6) {
+        phase_row(P, slot_p(0), 0, 0);
+        phase_row(Q, slot_p(0), 1, 0);
+    } else {
+        if (INTERIOR || j >= 1) phase_row(P, slot_p(1), 1, 0);
+        phase_row(Q, slot_p(0), 0, 0);
+    }
 #pragma unroll
     for (int k = 1; k < K; ++k) {
         // angles of the two steps that meet here (MODE 4: a or b) and of
@@ -862,17 +869,15 @@ struct Seg {
     bool store_lane;
     StripCoef c;
     Owned own;
-    // MODE 6: the warp's lower slab z (even), its index in the CTA, the Z
-    // exchange buffers, and which of its two slabs (z, z + 1) it writes
+    // MODE 6: the warp's lower slab z (even), its index in the CTA, and
+    // which of its two slabs (z, z + 1) it writes
     int z, w;
-    float4 *zx;
     bool store_a, store_b;
 };
 
 // MODE 6: where a warp sits in its CTA's block of slabs.
 struct Slab3 {
     int z = 0, w = 0, ytma = 0;
-    float4 *zx = nullptr;
     bool store_a = true, store_b = true;
 };
 
@@ -905,13 +910,16 @@ __device__ __forceinline__ bool wait_b(const WarpRings &r, int j, uint64_t limit
     return mbar_wait(&r.bar_b[L % NSB], (uint32_t)(L / NSB) & 1u, limit);
 }
 
+// MODE 6 (TWO) loads rows 2j - 1 and 2j of the range (a row below or past
+// the grid is off-grid in the pipeline, whatever it reads: zeros, or a row
+// of the neighbouring slab).
 template <int K, int PP = 2, bool TWO = false>
 __device__ __forceinline__ void issue_phase(WarpRings &r, const Seg &s, int pos, int j)
 {
     constexpr int PSLOT = Cfg<K, PP>::PSLOT;
     mbar_expect_tx(&r.bar_p[pos], PSLOT);
     unsigned char *dst = r.ring_p + pos * PSLOT;
-    const int y = s.ytma + s.Ys + 2 * j;
+    const int y = s.ytma + s.Ys + 2 * j - (TWO ? 1 : 0);
     tma_load_pair(dst, s.tm_phase, s.XL, y, &r.bar_p[pos]);
     if constexpr (TWO) tma_load_pair(dst + PSLOT / 2, s.tm_phase, s.XL, y + s.yslab, &r.bar_p[pos]);
 }
@@ -920,12 +928,17 @@ __device__ __forceinline__ void issue_phase(WarpRings &r, const Seg &s, int pos,
 // holds at the same y; warp w holds slabs z = z_w (even, in .a) and z + 1
 // (in .b).  Even Z pairs (z, z + 1) lie inside a warp: a register rotation
 // (lifting form).  Odd pairs (z + 1, z + 2) and (z - 1, z) join neighbouring
-// warps: each warp puts its rows in exchange buffer `zbuf`, the CTA meets at
-// a barrier, and each warp updates its own members from their partners' old
-// values in the versine form (a' = a - g a + i s b).  The two buffers
-// alternate, so that a warp writing the next exchange cannot overwrite rows
-// another warp still reads (it has passed the next barrier first).  A pair
-// needs both slabs on the grid and both in the CTA.
+// warps: each warp puts its rows in an exchange buffer, the CTA meets at a
+// barrier, and each warp updates its own members from their partners' old
+// values in the versine form (a' = a - g a + i s b).  A pair needs both slabs
+// on the grid and both in the CTA.
+//
+// The buffers are ring slots the warp has just consumed, at the same place in
+// every warp's rings (the warps walk the same row pairs): the first exchange
+// of row pair j goes through its state slot, whose refill is issued after
+// the second barrier; the second through its phase slot, whose refill waits
+// for the first barrier of row pair j + 1 (or the barrier that ends the
+// segment).  So no warp overwrites rows another warp still reads.
 __device__ __forceinline__ bool on_grid(int z, const KParams &p) { return z >= 0 && z < p.nz; }
 
 template <bool PACKED>
@@ -936,14 +949,16 @@ __device__ __forceinline__ void z_even(Frag2 &r0, Frag2 &r1, const Seg &s, const
     y_pair<PACKED>(r1.a, r1.b, v ? p.t1 : 0.f, v ? p.s1 : 0.f);
 }
 
-// The barrier of the exchange also combines the warps' `fail` flags: it
-// returns true, in every warp, if any warp of the CTA passed true.
-template <int NW>
+// `mine` is this warp's buffer (256 float4 = 4 KiB); the neighbours' lie
+// WSTRIDE float4 away.  The barrier of the exchange also combines the warps'
+// `fail` flags: it returns true, in every warp, if any warp of the CTA passed
+// true.  The buffer's later refill is a TMA write (the async proxy), so each
+// lane fences its generic writes before the barrier.
+template <int NW, int WSTRIDE>
 __device__ __forceinline__ bool z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const KParams &p,
-                                      int &zbuf, bool fail)
+                                      float4 *mine, bool fail)
 {
     const int lane = s.lane;
-    float4 *mine = s.zx + (zbuf * NW + s.w) * 256;
     mine[lane] = r0.a.re;
     mine[32 + lane] = r0.a.im;
     mine[64 + lane] = r1.a.re;
@@ -952,6 +967,7 @@ __device__ __forceinline__ bool z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const 
     mine[160 + lane] = r0.b.im;
     mine[192 + lane] = r1.b.re;
     mine[224 + lane] = r1.b.im;
+    fence_proxy_async();
     const bool any_fail = __syncthreads_or(fail);
     const float g = p.g1, sn = p.s1;
     const float2 ng = make_float2(-g, -g), ns = make_float2(-sn, -sn), ps = make_float2(sn, sn);
@@ -966,17 +982,16 @@ __device__ __forceinline__ bool z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const 
     };
     // slab z + 1 with the next warp's slab z + 2 (its .a rows)
     if (s.w + 1 < NW && on_grid(s.z + 1, p) && on_grid(s.z + 2, p)) {
-        const float4 *q = s.zx + (zbuf * NW + s.w + 1) * 256;
+        const float4 *q = mine + WSTRIDE;
         one(r0.b, q, 0);
         one(r1.b, q, 1);
     }
     // slab z with the previous warp's slab z - 1 (its .b rows)
     if (s.w > 0 && on_grid(s.z - 1, p) && on_grid(s.z, p)) {
-        const float4 *q = s.zx + (zbuf * NW + s.w - 1) * 256 + 128;
+        const float4 *q = mine - WSTRIDE + 128;
         one(r0.a, q, 0);
         one(r1.a, q, 1);
     }
-    zbuf ^= 1;
     return any_fail;
 }
 
@@ -1054,21 +1069,32 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     }
     // MODE 6: a 3-D step is Ze Zo [the 2-D step] Zo Ze (Z factors commute
     // with X and Y factors): the rows entering the pipeline take Ze, Zo, the
-    // rows leaving it take Zo, Ze.  Each row pair has two exchanges, so
-    // its first one uses buffer 0 again: the last reads of that buffer, in
-    // the previous row pair's first exchange, are behind this warp's and
-    // every other warp's second barrier since.
-    int zbuf = 0;
+    // rows leaving it take Zo, Ze.  The exchanges go through this row pair's
+    // state slot and then its phase slot (see z_odd).
+    constexpr int WSTRIDE = C::WARP_SMEM / 16;
     if constexpr (MODE == 6) {
         z_even<C::PACKED>(a, b, s, p);
-        if (z_odd<C::WPC>(a, b, s, p, zbuf, !ok)) return give_up();
+        float4 *xs = reinterpret_cast<float4 *>(r.ring_s + r.pos_s * C::SSLOT);
+        if (z_odd<C::WPC, WSTRIDE>(a, b, s, p, xs, !ok)) return give_up();
+        // every warp has read the previous row pair's second exchange, in its
+        // phase slot: refill that slot with row pair j - 1 + NSP
+        const int jq = j - 1 + NSP;
+        if (j >= 1 && jq < s.n_iter) {
+            if (lane == 0) {
+                fence_proxy_async();
+                issue_phase<K, phase_planes(MODE), true>(r, s, r.pos_p == 0 ? NSP - 1 : r.pos_p - 1,
+                                                         jq);
+            }
+            iss.p += 1;
+        }
     }
     const int yin = s.Ys + 2 * j;
     S O0, O1;
     pipeline_step<K, INTERIOR, MODE>(cin, cout, a, b, yin, j, r.ring_p, r.pos_p, r.ring_b,
                                      r.cnt_b, s.c, p, lane, s.own, O0, O1);
     if constexpr (MODE == 6) {
-        z_odd<C::WPC>(O0, O1, s, p, zbuf, false);
+        float4 *xp = reinterpret_cast<float4 *>(r.ring_p + r.pos_p * C::PSLOT);
+        z_odd<C::WPC, WSTRIDE>(O0, O1, s, p, xp, false);
         z_even<C::PACKED>(O0, O1, s, p);
     }
     const int yo = yin - 2 * K;
@@ -1084,11 +1110,12 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
         }
     }
     // state slot j and phase slot j-K are no longer read: refill them with
-    // row pairs j + NSS and j - K + NSP (the same ring positions); MODE 4
-    // also refills b slot j-3 with row pair j - 3 + NSB
+    // row pairs j + NSS and j - K + NSP (the same ring positions; MODE 6
+    // refills its phase slot at the next row pair); MODE 4 also refills b
+    // slot j-3 with row pair j - 3 + NSB
     __syncwarp();
     const int js = j + NSS, jp = j - K + NSP, jb = j - 3 + NSB;
-    const bool more_s = js < s.n_iter, more_p = j >= K && jp < s.n_iter;
+    const bool more_s = js < s.n_iter, more_p = MODE != 6 && j >= K && jp < s.n_iter;
     const bool more_b = MODE == 4 && j >= 3 && jb < s.n_iter;
     if (lane == 0 && (more_s || more_p || more_b)) {
         fence_proxy_async();
@@ -1128,7 +1155,6 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
     s.yslab = p.ny;
     s.z = sl.z;
     s.w = sl.w;
-    s.zx = sl.zx;
     s.store_a = sl.store_a;
     s.store_b = sl.store_b;
     s.lane = lane;
@@ -1232,6 +1258,9 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
         r.cnt_b += s.n_iter;
     }
     if constexpr (C::GST_BYTES > 0) cp_async_wait_all();
+    // MODE 6: the other warps may still read this segment's last exchange in
+    // this warp's phase slot, which the next segment's first copies refill
+    if constexpr (MODE == 6) __syncthreads();
     __syncwarp();
     return true;
 }
@@ -1294,12 +1323,10 @@ fused3d_kernel(const __grid_constant__ CUtensorMap tm_state,
     using C = CfgM<K, 6>;
     constexpr int NW = C::WPC, VZ = 2 * NW - 4;
     static_assert(VZ > 0 && VZ % 2 == 0, "the block's first slab must stay even");
+    static_assert(NW <= 16, "the host's row-coordinate guard assumes at most 16 warps");
     extern __shared__ unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpRings r = carve_rings<K, phase_planes(6), false, state_planes(6), 6>(smem_raw, warp, lane);
-    const uint32_t base_addr = smem_addr(smem_raw);
-    const uint32_t slots_off = ((base_addr + NW * C::NBAR * 8 + 1023u) & ~1023u) - base_addr;
-    float4 *zx = reinterpret_cast<float4 *>(smem_raw + slots_off + (size_t)NW * C::WARP_SMEM);
     const int64_t slab = (int64_t)p.ny * p.pitch;
     for (int64_t u = blockIdx.x; u < p.units; u += gridDim.x) {
         const int zb = (int)(u % p.n_zblocks);
@@ -1312,7 +1339,6 @@ fused3d_kernel(const __grid_constant__ CUtensorMap tm_state,
         sl.z = zb * VZ - 2 + 2 * warp;
         sl.w = warp;
         sl.ytma = sl.z * p.ny;
-        sl.zx = zx;
         const bool inner = warp >= 1 && warp < NW - 1;
         sl.store_a = inner && sl.z >= 0 && sl.z < p.nz;
         sl.store_b = inner && sl.z + 1 >= 0 && sl.z + 1 < p.nz;

@@ -127,7 +127,7 @@ cudaError_t launch_fused_u4(const FusedLaunch &a, cudaStream_t st);
 // One 3-D step Xe Xo Ye Yo Ze Zo P Zo Ze Yo Ye Xo Xe over an nx x ny x nz
 // FP32 grid in one HBM round trip: a.ny is the rows of one slab, tm_state
 // and tm_phase map all ny * nz rows (slab after slab), out_re, out_im take
-// the result.  Needs (nz + 16) * ny < 2^31.
+// the result.  Needs (nz + 32) * ny < 2^31.
 cudaError_t launch_fused3d(const FusedLaunch &a, int nz, cudaStream_t st);
 
 // Device-resident description of one FP32 grid for the multi-grid launch

@@ -80,13 +80,14 @@ def test_fp64_launch_count():
         g.close()
 
 
-# nz across the z-blocks of 12 stored slabs (2, 3, 11, 12, 13, 24, 25, 40,
-# 150), odd and even ny (1 and 2 included), strips of 120 columns with a
-# ragged last one (121, 241, 257)
+# nz across the z-blocks of 20 stored slabs (19, 20, 21, 40, 41, 150) and of
+# 12 (11, 12, 13, 24, 25), odd and even ny (1 and 2 included), strips of 120
+# columns with a ragged last one (121, 241, 257)
 @pytest.mark.parametrize("nx,ny,nz", [(96, 64, 40), (130, 66, 17), (33, 2, 9), (257, 130, 5),
                                       (64, 32, 150), (20, 8, 2), (5, 11, 7), (121, 7, 13),
                                       (40, 9, 3), (3, 1, 25), (241, 5, 24), (17, 12, 11),
-                                      (16, 3, 12)])
+                                      (16, 3, 12), (9, 4, 19), (48, 10, 20), (35, 6, 21),
+                                      (24, 5, 41)])
 @pytest.mark.parametrize("path", ["fused", "plain"])
 def test_fp32_matches_oracle(nx, ny, nz, path):
     """Every side length and block edge of the fused 3-D step against the
