@@ -188,11 +188,16 @@ struct Cfg {
     // depth but 2 (where the scalar form measured faster), 2 always
     static constexpr bool PACKED = TS_FUSED_FFMA2 == 2 || (TS_FUSED_FFMA2 == 1 && K != 2);
     static constexpr int NSS = PF + 1;
-    // phase ring: step k of iteration j reads the rows of pair j - k and of
-    // pair j - k - 1, so the ring holds K + 1 pairs and the PF ahead; MODE 6
-    // loads each slot one row earlier (rows 2j - 1 and 2j of the pair's
-    // range), which puts both rows of a step in one slot
-    static constexpr int NSP = PF + K + (M == 6 ? 0 : 1);
+    // phase ring: the phase of step k at iteration j falls on rows 2(j - k)
+    // - 1 and 2(j - k) of the range, so each slot is loaded one row earlier
+    // than the state's (PSHIFT): a step then reads one slot, and the ring
+    // holds K pairs and the PF ahead.  MODE 4 keeps slots on the state's
+    // rows (a step reads pairs j - k - 1 and j - k: K + 1 pairs), as its b
+    // ring does, and so does depth 1 outside MODE 6 (with the slot saved,
+    // more depth-1 warps fit in shared memory, and they measured 11 % slower:
+    // their halo columns are shared through L2 by warps that keep pace).
+    static constexpr bool PSHIFT = M == 6 || (M != 4 && K >= 2);
+    static constexpr int NSP = PF + K + (PSHIFT ? 0 : 1);
     static constexpr int HALO = ((2 * K + 3) / 4) * 4;
     static constexpr int VALID = FUSED_BOX_COLS - 2 * HALO;
     // a phase slot holds (gamma_V, s_V) and, with a drive, the V1 rows too
@@ -742,9 +747,9 @@ __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2
             if constexpr (MODE == 3) drive4<C::PACKED>(X, lds4(sp, 2, row, lane), p.adt[k]);
         }
     };
-    // phase of step 0 on rows (y1, y1+1): slot j-1 row 1, slot j row 0
-    // (MODE 6: rows 0 and 1 of slot j)
-    if constexpr (MODE == 6) {
+    // phase of step 0 on rows (y1, y1+1): rows 0 and 1 of slot j (without
+    // PSHIFT: slot j-1 row 1, slot j row 0)
+    if constexpr (C::PSHIFT) {
         phase_row(P, slot_p(0), 0, 0);
         phase_row(Q, slot_p(0), 1, 0);
     } else {
@@ -787,12 +792,20 @@ __device__ __forceinline__ void pipeline_step(const S (&cin)[2 * K], S (&cout)[2
         Q = P2;
         y1 -= 2;
         if constexpr (MODE == 5) adj_step<K>(k, P, Q, y1, carP, carQ, w, p);
-        // phase of step k on rows (y1, y1+1): slot j-k-1 row 1, slot j-k row 0
-        // (MODE 4: the b substep's table comes from the b ring; MODE 5: the
-        // conjugate phase, sine -s_V)
+        // phase of step k on rows (y1, y1+1): rows 0 and 1 of slot j-k
+        // (without PSHIFT, MODE 4: slot j-k-1 row 1, slot j-k row 0, and the
+        // b substep's table from the b ring; MODE 5: the conjugate phase,
+        // sine -s_V)
         auto slot_k = [&](int back) { return bk ? slot_b(back) : slot_p(back); };
-        if (INTERIOR || j - k - 1 >= 0) phase_row(P, slot_k(k + 1), 1, k);
-        if (INTERIOR || j - k >= 0) phase_row(Q, slot_k(k), 0, k);
+        if constexpr (C::PSHIFT) {
+            if (INTERIOR || j - k >= 0) {   // rows 0 and 1 of slot j-k
+                phase_row(P, slot_p(k), 0, k);
+                phase_row(Q, slot_p(k), 1, k);
+            }
+        } else {
+            if (INTERIOR || j - k - 1 >= 0) phase_row(P, slot_k(k + 1), 1, k);
+            if (INTERIOR || j - k >= 0) phase_row(Q, slot_k(k), 0, k);
+        }
     }
     // last step, second half: Yo aligned, Ye shifted, Xo, Xe
     {
@@ -910,16 +923,16 @@ __device__ __forceinline__ bool wait_b(const WarpRings &r, int j, uint64_t limit
     return mbar_wait(&r.bar_b[L % NSB], (uint32_t)(L / NSB) & 1u, limit);
 }
 
-// MODE 6 (TWO) loads rows 2j - 1 and 2j of the range (a row below or past
-// the grid is off-grid in the pipeline, whatever it reads: zeros, or a row
-// of the neighbouring slab).
-template <int K, int PP = 2, bool TWO = false>
+// SHIFT: rows 2j - 1 and 2j of the range instead of 2j and 2j + 1 (a row
+// outside the grid is off-grid in the pipeline, whatever it reads: zeros,
+// or for MODE 6 a row of the neighbouring slab).
+template <int K, int PP, bool TWO, bool SHIFT>
 __device__ __forceinline__ void issue_phase(WarpRings &r, const Seg &s, int pos, int j)
 {
     constexpr int PSLOT = Cfg<K, PP>::PSLOT;
     mbar_expect_tx(&r.bar_p[pos], PSLOT);
     unsigned char *dst = r.ring_p + pos * PSLOT;
-    const int y = s.ytma + s.Ys + 2 * j - (TWO ? 1 : 0);
+    const int y = s.ytma + s.Ys + 2 * j - (SHIFT ? 1 : 0);
     tma_load_pair(dst, s.tm_phase, s.XL, y, &r.bar_p[pos]);
     if constexpr (TWO) tma_load_pair(dst + PSLOT / 2, s.tm_phase, s.XL, y + s.yslab, &r.bar_p[pos]);
 }
@@ -1082,8 +1095,8 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
         if (j >= 1 && jq < s.n_iter) {
             if (lane == 0) {
                 fence_proxy_async();
-                issue_phase<K, phase_planes(MODE), true>(r, s, r.pos_p == 0 ? NSP - 1 : r.pos_p - 1,
-                                                         jq);
+                issue_phase<K, phase_planes(MODE), true, true>(
+                    r, s, r.pos_p == 0 ? NSP - 1 : r.pos_p - 1, jq);
             }
             iss.p += 1;
         }
@@ -1109,19 +1122,22 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
             store_rows(O0, O1, p.out_re, p.out_im, yo);
         }
     }
-    // state slot j and phase slot j-K are no longer read: refill them with
-    // row pairs j + NSS and j - K + NSP (the same ring positions; MODE 6
-    // refills its phase slot at the next row pair); MODE 4 also refills b
-    // slot j-3 with row pair j - 3 + NSB
+    // state slot j and the oldest phase slot read here (j - K + 1, or j - K
+    // without PSHIFT) are no longer read: refill them with row pairs j + NSS
+    // and that slot's pair + NSP (the same ring positions; MODE 6 refills its
+    // phase slot at the next row pair); MODE 4 also refills b slot j-3 with
+    // row pair j - 3 + NSB
     __syncwarp();
-    const int js = j + NSS, jp = j - K + NSP, jb = j - 3 + NSB;
-    const bool more_s = js < s.n_iter, more_p = MODE != 6 && j >= K && jp < s.n_iter;
+    constexpr int PBACK = C::PSHIFT ? K - 1 : K;
+    const int js = j + NSS, jp = j - PBACK + NSP, jb = j - 3 + NSB;
+    const bool more_s = js < s.n_iter, more_p = MODE != 6 && j >= PBACK && jp < s.n_iter;
     const bool more_b = MODE == 4 && j >= 3 && jb < s.n_iter;
     if (lane == 0 && (more_s || more_p || more_b)) {
         fence_proxy_async();
         if (more_s) issue_state<C::SSLOT, MODE == 6>(r, s, r.pos_s, js);
         if (more_p)
-            issue_phase<K, phase_planes(MODE), MODE == 6>(r, s, r.pos_p - K < 0 ? r.pos_p - K + NSP : r.pos_p - K, jp);
+            issue_phase<K, phase_planes(MODE), MODE == 6, C::PSHIFT>(
+                r, s, r.pos_p - PBACK < 0 ? r.pos_p - PBACK + NSP : r.pos_p - PBACK, jp);
         if constexpr (MODE == 4) {
             if (more_b) issue_b<NSB>(r, s, jb);   // the slot row pair j - 3 leaves
         }
@@ -1189,7 +1205,7 @@ __device__ __forceinline__ bool run_segment(WarpRings &r, const CUtensorMap *tm_
         fence_proxy_async();
         for (int j = 0; j < n_pro_p; ++j) {
             if (j < n_pro_s) issue_state<C::SSLOT, MODE == 6>(r, s, (r.pos_s + j) % NSS, j);
-            issue_phase<K, phase_planes(MODE), MODE == 6>(r, s, (r.pos_p + j) % NSP, j);
+            issue_phase<K, phase_planes(MODE), MODE == 6, C::PSHIFT>(r, s, (r.pos_p + j) % NSP, j);
             if constexpr (MODE == 4) {
                 if (j < n_pro_b) issue_b<NSB>(r, s, j);
             }
