@@ -428,22 +428,25 @@ __device__ __forceinline__ void phase4(Frag2 &f, float4 g, float4 s)
 // Drive phase exp(-i a dt V1) of one row of the lane (time-dependent
 // potential): adt = a_n dt of the step, v1 = the row's V1 values, so the
 // angle of a site is phi = adt V1.  With u = phi^2, sin(phi) = phi P(u) and
-// 1 - cos(phi) = u Q(u), P and Q the Taylor series of sin(x)/x and
-// (1 - cos x)/x^2 in u through u^4: the truncation stays under 3e-9 for
-// |phi| <= 0.8, and an FP32 emulation of this evaluation gives relative
-// errors under 1.5e-7.  (A second, shorter series for smaller angles
-// measured slower: the kernel is bound by instruction issue and
-// instruction-cache misses, not by these operations.)
+// 1 - cos(phi) = u Q(u), P and Q cubics in u fitted to sin(x)/x and
+// (1 - cos x)/x^2 on u in [0, 0.64] (|phi| <= 0.8) by the Remez exchange
+// (equal-ripple absolute error) and rounded to FP32: they are within 6.8e-9
+// and 6.7e-10 of the functions there, and an FP32 emulation of this
+// evaluation gives relative errors under 1.5e-7 in both results, as the
+// Taylor polynomials through u^4 did with one more FMA each (3 % slower: the
+// kernel is bound by instruction issue).  (A second, shorter series for
+// smaller angles measured slower too.)
+constexpr float DRIVE_P1 = -0x1.55553ep-3f, DRIVE_P2 = 0x1.11055ep-7f, DRIVE_P3 = -0x1.98c40ap-13f;
+constexpr float DRIVE_Q1 = -0x1.55554cp-5f, DRIVE_Q2 = 0x1.6c0d6p-10f, DRIVE_Q3 = -0x1.9a398ap-16f;
+
 __device__ __forceinline__ void versine_phi2(float2 phi, float2 &g, float2 &s)
 {
     auto c2 = [](float v) { return make_float2(v, v); };
     const float2 u = __fmul2_rn(phi, phi);
-    float2 P = __ffma2_rn(u, c2(1.0f / 362880.0f), c2(-1.0f / 5040.0f));
-    float2 Q = __ffma2_rn(u, c2(1.0f / 3628800.0f), c2(-1.0f / 40320.0f));
-    P = __ffma2_rn(u, P, c2(1.0f / 120.0f));
-    Q = __ffma2_rn(u, Q, c2(1.0f / 720.0f));
-    P = __ffma2_rn(u, P, c2(-1.0f / 6.0f));
-    Q = __ffma2_rn(u, Q, c2(-1.0f / 24.0f));
+    float2 P = __ffma2_rn(u, c2(DRIVE_P3), c2(DRIVE_P2));
+    float2 Q = __ffma2_rn(u, c2(DRIVE_Q3), c2(DRIVE_Q2));
+    P = __ffma2_rn(u, P, c2(DRIVE_P1));
+    Q = __ffma2_rn(u, Q, c2(DRIVE_Q1));
     P = __ffma2_rn(u, P, c2(1.0f));
     Q = __ffma2_rn(u, Q, c2(0.5f));
     s = __fmul2_rn(phi, P);
@@ -454,12 +457,10 @@ __device__ __forceinline__ void versine_phi2(float2 phi, float2 &g, float2 &s)
 __device__ __forceinline__ void versine_phi(float phi, float &g, float &s)
 {
     const float u = phi * phi;
-    float P = fmaf(u, 1.0f / 362880.0f, -1.0f / 5040.0f);
-    float Q = fmaf(u, 1.0f / 3628800.0f, -1.0f / 40320.0f);
-    P = fmaf(u, P, 1.0f / 120.0f);
-    Q = fmaf(u, Q, 1.0f / 720.0f);
-    P = fmaf(u, P, -1.0f / 6.0f);
-    Q = fmaf(u, Q, -1.0f / 24.0f);
+    float P = fmaf(u, DRIVE_P3, DRIVE_P2);
+    float Q = fmaf(u, DRIVE_Q3, DRIVE_Q2);
+    P = fmaf(u, P, DRIVE_P1);
+    Q = fmaf(u, Q, DRIVE_Q1);
     P = fmaf(u, P, 1.0f);
     Q = fmaf(u, Q, 0.5f);
     s = phi * P;
@@ -490,7 +491,13 @@ __device__ __forceinline__ void drive4(Frag &f, float4 v1, float adt)
     // angle in the warp is at most 0.8 -- decided for the whole warp, so that
     // the branch does not diverge (all lanes are converged here); larger
     // angles take the reduced path, on the half angle
-    const float4 phi = make_float4(adt * v1.x, adt * v1.y, adt * v1.z, adt * v1.w);
+    float4 phi;
+    if constexpr (PACKED) {
+        const float2 a2 = make_float2(adt, adt);
+        phi = join2(__fmul2_rn(a2, lo2(v1)), __fmul2_rn(a2, hi2(v1)));
+    } else {
+        phi = make_float4(adt * v1.x, adt * v1.y, adt * v1.z, adt * v1.w);
+    }
     float4 g, s;
     const float m = fmaxf(fmaxf(fabsf(phi.x), fabsf(phi.y)), fmaxf(fabsf(phi.z), fabsf(phi.w)));
     auto all = [](bool b) { return TS_FUSED_DRIVE_WARP_BRANCH ? __all_sync(FULL, b) : b; };
@@ -1024,8 +1031,14 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     using C = CfgM<K, MODE>;
     constexpr int NSS = C::NSS, NSP = C::NSP, NSB = C::NSB;
     const int lane = s.lane;
+    // MODE 6 waits for its phase slot just before the phase point: the slot
+    // was refilled only after the previous row pair's first barrier (it
+    // carried that row pair's second exchange), and a wait at the start of
+    // the row pair cost 4 %.  A wait that gives up is combined over the CTA
+    // at the second exchange's barrier.
+    constexpr bool LATE_P = MODE == 6;
     bool ok = mbar_wait(&r.bar_s[r.pos_s], r.par_s, WAIT_LIMIT_NS) &&
-              mbar_wait(&r.bar_p[r.pos_p], r.par_p, WAIT_LIMIT_NS);
+              (LATE_P || mbar_wait(&r.bar_p[r.pos_p], r.par_p, WAIT_LIMIT_NS));
     if constexpr (MODE == 4)   // row pair j - 2's b rows, first read now
         ok = ok && (j < 2 || wait_b<NSB>(r, j - 2, WAIT_LIMIT_NS));
     ok = __all_sync(FULL, ok);
@@ -1048,9 +1061,9 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
         return false;
     };
     // MODE 6: the CTA's warps meet at barriers, so they give up together, at
-    // the first barrier of the row pair (the Z exchange below); until then a
-    // warp whose wait gave up computes on stale slot contents, which is
-    // harmless since nothing of it is stored
+    // the barrier of the row pair's first Z exchange (state wait) or second
+    // (phase wait); until then a warp whose wait gave up computes on stale
+    // slot contents, which is harmless since nothing of it is stored
     if (MODE != 6 && !ok) return give_up();
     const unsigned char *sj = r.ring_s + r.pos_s * C::SSLOT;
     // rows 0 and 1 of a state slot's planes (re, im) -- and (re, im) of the
@@ -1102,12 +1115,15 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
         }
     }
     const int yin = s.Ys + 2 * j;
+    bool okp = true;
+    if constexpr (LATE_P)
+        okp = __all_sync(FULL, mbar_wait(&r.bar_p[r.pos_p], r.par_p, WAIT_LIMIT_NS));
     S O0, O1;
     pipeline_step<K, INTERIOR, MODE>(cin, cout, a, b, yin, j, r.ring_p, r.pos_p, r.ring_b,
                                      r.cnt_b, s.c, p, lane, s.own, O0, O1);
     if constexpr (MODE == 6) {
         float4 *xp = reinterpret_cast<float4 *>(r.ring_p + r.pos_p * C::PSLOT);
-        z_odd<C::WPC, WSTRIDE>(O0, O1, s, p, xp, false);
+        if (z_odd<C::WPC, WSTRIDE>(O0, O1, s, p, xp, !okp)) return give_up();
         z_even<C::PACKED>(O0, O1, s, p);
     }
     const int yo = yin - 2 * K;
