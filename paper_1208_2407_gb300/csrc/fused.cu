@@ -973,10 +973,12 @@ __device__ __forceinline__ void z_even(Frag2 &r0, Frag2 &r1, const Seg &s, const
 // WSTRIDE float4 away.  The barrier of the exchange also combines the warps'
 // `fail` flags: it returns true, in every warp, if any warp of the CTA passed
 // true.  The buffer's later refill is a TMA write (the async proxy), so each
-// lane fences its generic writes before the barrier.
-template <int NW, int WSTRIDE>
+// lane fences its generic writes before the barrier.  `after` runs right
+// after the barrier unless a warp failed: the slots that the barrier frees
+// are refilled there, before this exchange's reads and updates.
+template <int NW, int WSTRIDE, typename F>
 __device__ __forceinline__ bool z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const KParams &p,
-                                      float4 *mine, bool fail)
+                                      float4 *mine, bool fail, F &&after)
 {
     const int lane = s.lane;
     mine[lane] = r0.a.re;
@@ -989,6 +991,8 @@ __device__ __forceinline__ bool z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const 
     mine[224 + lane] = r1.b.im;
     fence_proxy_async();
     const bool any_fail = __syncthreads_or(fail);
+    if (any_fail) return true;
+    after();
     const float g = p.g1, sn = p.s1;
     const float2 ng = make_float2(-g, -g), ns = make_float2(-sn, -sn), ps = make_float2(sn, sn);
     auto one = [&](Frag &f, const float4 *q, int row) {   // f <- f - g f + i s q, four columns
@@ -1012,7 +1016,7 @@ __device__ __forceinline__ bool z_odd(Frag2 &r0, Frag2 &r1, const Seg &s, const 
         one(r0.a, q, 0);
         one(r1.a, q, 1);
     }
-    return any_fail;
+    return false;
 }
 
 // Row pair j of a segment: wait for its slots, run the pipeline, store the
@@ -1101,18 +1105,23 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     if constexpr (MODE == 6) {
         z_even<C::PACKED>(a, b, s, p);
         float4 *xs = reinterpret_cast<float4 *>(r.ring_s + r.pos_s * C::SSLOT);
-        if (z_odd<C::WPC, WSTRIDE>(a, b, s, p, xs, !ok)) return give_up();
-        // every warp has read the previous row pair's second exchange, in its
-        // phase slot: refill that slot with row pair j - 1 + NSP
-        const int jq = j - 1 + NSP;
-        if (j >= 1 && jq < s.n_iter) {
-            if (lane == 0) {
-                fence_proxy_async();
-                issue_phase<K, phase_planes(MODE), true, true>(
-                    r, s, r.pos_p == 0 ? NSP - 1 : r.pos_p - 1, jq);
-            }
-            iss.p += 1;
-        }
+        // past this barrier every warp has read the previous row pair's
+        // second exchange, in its phase slot: refill that slot with row pair
+        // j - 1 + NSP.  (Both 3-D refills are issued right after the barrier
+        // that frees their slot; issued after the exchange's updates and at
+        // the end of the row pair, they measured 5 % slower.)
+        if (z_odd<C::WPC, WSTRIDE>(a, b, s, p, xs, !ok, [&]() {
+                const int jq = j - 1 + NSP;
+                if (j >= 1 && jq < s.n_iter) {
+                    if (lane == 0) {
+                        fence_proxy_async();
+                        issue_phase<K, phase_planes(MODE), true, true>(
+                            r, s, r.pos_p == 0 ? NSP - 1 : r.pos_p - 1, jq);
+                    }
+                    iss.p += 1;
+                }
+            }))
+            return give_up();
     }
     const int yin = s.Ys + 2 * j;
     bool okp = true;
@@ -1123,7 +1132,19 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
                                      r.cnt_b, s.c, p, lane, s.own, O0, O1);
     if constexpr (MODE == 6) {
         float4 *xp = reinterpret_cast<float4 *>(r.ring_p + r.pos_p * C::PSLOT);
-        if (z_odd<C::WPC, WSTRIDE>(O0, O1, s, p, xp, !okp)) return give_up();
+        // past this barrier every warp has read this row pair's first
+        // exchange, in its state slot: refill that slot with row pair j + NSS
+        if (z_odd<C::WPC, WSTRIDE>(O0, O1, s, p, xp, !okp, [&]() {
+                const int js = j + NSS;
+                if (js < s.n_iter) {
+                    if (lane == 0) {
+                        fence_proxy_async();
+                        issue_state<C::SSLOT, true>(r, s, r.pos_s, js);
+                    }
+                    iss.s += 1;
+                }
+            }))
+            return give_up();
         z_even<C::PACKED>(O0, O1, s, p);
     }
     const int yo = yin - 2 * K;
@@ -1140,13 +1161,15 @@ __device__ __forceinline__ bool row_pair(WarpRings &r, const Seg &s, const KPara
     }
     // state slot j and the oldest phase slot read here (j - K + 1, or j - K
     // without PSHIFT) are no longer read: refill them with row pairs j + NSS
-    // and that slot's pair + NSP (the same ring positions; MODE 6 refills its
-    // phase slot at the next row pair); MODE 4 also refills b slot j-3 with
-    // row pair j - 3 + NSB
+    // and that slot's pair + NSP (the same ring positions; MODE 6 refilled
+    // its state slot at the second exchange and refills its phase slot at
+    // the next row pair's first); MODE 4 also refills b slot j-3 with row
+    // pair j - 3 + NSB
     __syncwarp();
     constexpr int PBACK = C::PSHIFT ? K - 1 : K;
     const int js = j + NSS, jp = j - PBACK + NSP, jb = j - 3 + NSB;
-    const bool more_s = js < s.n_iter, more_p = MODE != 6 && j >= PBACK && jp < s.n_iter;
+    const bool more_s = MODE != 6 && js < s.n_iter;
+    const bool more_p = MODE != 6 && j >= PBACK && jp < s.n_iter;
     const bool more_b = MODE == 4 && j >= 3 && jb < s.n_iter;
     if (lane == 0 && (more_s || more_p || more_b)) {
         fence_proxy_async();
