@@ -29,8 +29,10 @@
 //    at an odd row, is "aligned" and completes at once; the other kind waits
 //    for the next row and carries one row in registers.  The output trails
 //    the input by 2K rows; a row range reads 2K halo rows above and below.
-//  - The phase of step k is read from the slot ring where its rows still sit
-//    (the ring keeps K slots behind the current one).
+//  - The phase of step k is read from the phase ring, which keeps the slots of
+//    the K most recent row pairs; its slots are loaded one row earlier than
+//    the state's, so each step's phase point reads one slot (the fourth-order
+//    kernel and depth 1 keep the state's rows and one slot more).
 // Grid-edge sites: TMA fills rows/columns outside the grid with zeros, and a
 // pair whose partner lies outside the grid gets coefficients (0, 0), i.e. the
 // identity (open boundaries: the unpaired site is unchanged).
